@@ -1,0 +1,134 @@
+"""Seeded synthetic inputs for the stable integer sort.
+
+Shared by the oracle side and the CUDA side (tests, smoke check, benchmark);
+holds none of the sort's arithmetic.  Values are a pure function of
+(seed, record index) -- see ``gen.c`` for the families -- so every input is
+reproducible on any machine and with any thread count.
+"""
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "gen.c")
+_SO = os.path.join(_HERE, "_build", "libgen.so")
+_lib = None
+
+UNIFORM, ZIPF, ZIPF_HASHED, EXP, BITEXP, DISTINCT, HEAVYMIX, SKEWMIX, \
+    BEXP_PAPER, UNIF_MU = range(10)
+
+
+def build(force=False):
+    if (not force and os.path.exists(_SO)
+            and os.path.getmtime(_SO) >= os.path.getmtime(_SRC)):
+        return _SO
+    os.makedirs(os.path.dirname(_SO), exist_ok=True)
+    tmp = _SO + ".tmp%d" % os.getpid()
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC",
+                           "-pthread", _SRC, "-o", tmp, "-lm"])
+    os.replace(tmp, _SO)
+    return _SO
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        L = ctypes.CDLL(build())
+        L.gen_keys.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                               ctypes.c_double, ctypes.c_uint64, ctypes.c_int64,
+                               ctypes.c_int64, ctypes.c_void_p, ctypes.c_int]
+        L.gen_keys.restype = ctypes.c_int
+        L.gen_iota.argtypes = [ctypes.c_int, ctypes.c_int64, ctypes.c_int64,
+                               ctypes.c_void_p]
+        L.gen_iota.restype = ctypes.c_int
+        L.gen_rng.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64]
+        L.gen_rng.restype = ctypes.c_uint64
+        L.gen_segment_sizes.argtypes = [ctypes.c_uint64, ctypes.c_int64,
+                                        ctypes.c_double, ctypes.c_double,
+                                        ctypes.c_void_p, ctypes.c_void_p]
+        L.gen_segment_sizes.restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def fill_keys(out_ptr, n, kind, kbytes, seed, p1=0.0, p2=0.0, first=0,
+              nthreads=0):
+    """Write n keys of the family into host memory at out_ptr."""
+    if lib().gen_keys(kind, kbytes, float(p1), float(p2), seed, first, n,
+                      out_ptr, nthreads):
+        raise ValueError("bad generator request")
+
+
+def keys(n, kind, dtype=np.uint32, seed=1, p1=0.0, p2=0.0, first=0,
+         nthreads=0):
+    dtype = np.dtype(dtype)
+    out = np.empty(n, dtype=dtype)
+    fill_keys(out.ctypes.data, n, kind, dtype.itemsize, seed, p1, p2, first,
+              nthreads)
+    return out
+
+
+def iota(n, dtype=np.uint32, first=0):
+    dtype = np.dtype(dtype)
+    out = np.empty(n, dtype=dtype)
+    lib().gen_iota(dtype.itemsize, first, n, out.ctypes.data)
+    return out
+
+
+def fill_iota(out_ptr, n, vbytes, first=0):
+    lib().gen_iota(vbytes, first, n, out_ptr)
+
+
+def rng(seed, stream, i):
+    return lib().gen_rng(seed, stream, i)
+
+
+def segment_sizes(nseg, lo, hi, seed=1):
+    sizes = np.empty(nseg, dtype=np.int64)
+    fam = np.empty(nseg, dtype=np.int32)
+    lib().gen_segment_sizes(seed, nseg, float(lo), float(hi), sizes.ctypes.data,
+                            fam.ctypes.data)
+    return sizes, fam
+
+
+# ---- the benchmark configurations ------------------------------------------
+# (name -> (kind, key dtype, p1, p2)); N = 1e9 universe for Zipf families.
+U32_FAMILIES = {
+    "uniform": (UNIFORM, np.uint32, 0.0, 0.0),
+    "zipf0.8": (ZIPF, np.uint32, 0.8, 1e9),
+    "zipf1.0": (ZIPF, np.uint32, 1.0, 1e9),
+    "zipf1.2": (ZIPF, np.uint32, 1.2, 1e9),
+    "zipf1.5": (ZIPF, np.uint32, 1.5, 1e9),
+    "zipf1.2hash": (ZIPF_HASHED, np.uint32, 1.2, 1e9),
+    "exp": (EXP, np.uint32, None, 0.0),       # rate = 10 / n, filled per n
+    "bitexp": (BITEXP, np.uint32, 0.0, 0.0),
+    "distinct10": (DISTINCT, np.uint32, 10, 0.0),
+    "bexp30": (BEXP_PAPER, np.uint32, 30, 0.0),
+    "unif1e3": (UNIF_MU, np.uint32, 1e3, 0.0),
+}
+U64_FAMILIES = {
+    "uniform": (UNIFORM, np.uint64, 0.0, 0.0),
+    "zipf1.2hash": (ZIPF_HASHED, np.uint64, 1.2, 1e9),
+    "heavymix": (HEAVYMIX, np.uint64, 0.5, 100),
+    "skewmix": (SKEWMIX, np.uint64, 0.0, 0.0),
+    "bitexp": (BITEXP, np.uint64, 0.0, 0.0),
+}
+
+
+def family(name, n, dtype=np.uint32, seed=1, nthreads=0):
+    table = U32_FAMILIES if np.dtype(dtype) == np.uint32 else U64_FAMILIES
+    kind, dt, p1, p2 = table[name]
+    if p1 is None:
+        p1 = 10.0 / max(n, 1)
+    return keys(n, kind, dt, seed, p1, p2, nthreads=nthreads)
+
+
+def fill_family(name, out_ptr, n, dtype=np.uint32, seed=1, nthreads=0):
+    table = U32_FAMILIES if np.dtype(dtype) == np.uint32 else U64_FAMILIES
+    kind, dt, p1, p2 = table[name]
+    if p1 is None:
+        p1 = 10.0 / max(n, 1)
+    fill_keys(out_ptr, n, kind, np.dtype(dt).itemsize, seed, p1, p2,
+              nthreads=nthreads)
