@@ -1,0 +1,339 @@
+"""Benchmark: stable sort of 10^9 uint32 key / uint32 value pairs (uniform
+keys, values = original index) on one GB300, through the dtsort C-ABI.
+
+One step = one complete sort of the whole array (sampling, every
+distribution level, the on-chip base case, dovetail merges).  Inputs are
+synthetic (seeded generator) and resident in HBM when a timed step starts; the
+pristine input is restored before every step (untimed, device to device), and
+at 8 GB per step the working set is far larger than L2.  Device time is taken
+with CUDA events on the sorting stream.
+
+Prints one JSON line (rank 0).  --impl reference times the CPU oracle on the
+host cores on a bounded sample of the same workload instead.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "sorted keys/s (10^9 keys, u32/u64 KV) and fraction of GB300 HBM roofline"
+# algorithmic bytes per record (key read for the level-0 histogram, then two
+# distribution passes and the on-chip base case, each reading and writing the
+# record): K + 3 * 2 * (K + V)
+B_ALG = {"u32kv": 4 + 3 * 2 * 8, "u64kv": 8 + 3 * 2 * 16, "u64": 8 + 3 * 2 * 8,
+         "u32": 4 + 3 * 2 * 4}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=1_000_000_000)
+    ap.add_argument("--dist", default="uniform")
+    ap.add_argument("--op", default="u32kv", choices=["u32kv", "u32", "u64kv", "u64"])
+    ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--cpu-sample", type=int, default=100_000_000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("clocks.sm,clocks.max.sm,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thr = threading.Thread(target=self._read, daemon=True)
+            self.thr.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 7:
+                self.rows.append(parts)
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            for nm, val in zip(names, r[3:7]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(self.rows)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def key_dtype(op):
+    return np.uint32 if op.startswith("u32") else np.uint64
+
+
+def sample_keys(args, count):
+    """The first `count` keys of the benchmark's seeded stream."""
+    import gen
+    kd = key_dtype(args.op)
+    table = gen.U32_FAMILIES if kd == np.uint32 else gen.U64_FAMILIES
+    kind, dt, p1, p2 = table[args.dist]
+    if p1 is None:  # the exponential's rate is fixed by the full n
+        p1 = 10.0 / args.n
+    return gen.keys(count, kind, kd, args.seed, p1, p2)
+
+
+def cpu_oracle_time(args, sample):
+    """The oracle, as it stands, on `sample` records, all host cores."""
+    import gen
+    import oracle
+    kd = key_dtype(args.op)
+    keys = sample_keys(args, sample)
+    vals = gen.iota(sample, kd) if args.op.endswith("kv") else None
+    cores = oracle.default_threads()
+    t0 = time.perf_counter()
+    oracle.stable_sort(keys, vals, nthreads=cores)
+    dt = time.perf_counter() - t0
+    return sample / dt, cores, dt
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import gen  # noqa: F401
+    sample = args.cpu_sample
+    times = []
+    cores = 0
+    for i in range(args.warmup + args.steps):
+        v, cores, dt = cpu_oracle_time(args, sample)
+        if i >= args.warmup:
+            times.append(dt)
+    t = statistics.mean(times)
+    value = sample / t
+    line = {"metric": METRIC, "value": value, "unit": "keys/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": args.op, "data": "synthetic",
+            "config": {"workload": "%s %s n=%d (oracle on a %d-record sample of the same "
+                                   "stream)" % (args.op, args.dist, args.n, sample),
+                       "n": args.n, "dist": args.dist},
+            "impl": "reference",
+            "cpu_baseline": {"value": value, "unit": "keys/s", "cores": cores,
+                             "kind": "oracle",
+                             "sample": "first %d records of the same seeded stream" % sample},
+            "e2e": {"value": value, "unit": "keys/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+
+    import gen
+    import paper_2401_00710_gb300 as dts
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as tdist
+        tdist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    kd = key_dtype(args.op)
+    kbytes = np.dtype(kd).itemsize
+    has_v = args.op.endswith("kv")
+    n = args.n
+    tdt = torch.int32 if kbytes == 4 else torch.int64
+    # inputs: generated on the host into pinned memory, one pristine device copy
+    hk = torch.empty(n, dtype=tdt, pin_memory=True)
+    gen.fill_family(args.dist, hk.data_ptr(), n, kd, seed=args.seed + rank)
+    hv = None
+    if has_v:
+        hv = torch.empty(n, dtype=tdt, pin_memory=True)
+        gen.fill_iota(hv.data_ptr(), n, kbytes)
+    pk = hk.to(dev)
+    pv = hv.to(dev) if has_v else None
+    k = torch.empty_like(pk)
+    v = torch.empty_like(pv) if has_v else None
+    op = {"u32kv": dts.DTSORT_OP_U32_KV, "u32": dts.DTSORT_OP_U32,
+          "u64kv": dts.DTSORT_OP_U64_KV, "u64": dts.DTSORT_OP_U64}[args.op]
+    h = dts.dtsort_create(local)
+    wsb = dts.dtsort_workspace_bytes(h, op, n)
+    ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    sp = stream.cuda_stream
+    fn = {dts.DTSORT_OP_U32_KV: dts.dtsort_u32_kv, dts.DTSORT_OP_U64_KV: dts.dtsort_u64_kv,
+          dts.DTSORT_OP_U32: dts.dtsort_u32, dts.DTSORT_OP_U64: dts.dtsort_u64}[op]
+
+    def sort_once(kp, vp):
+        if has_v:
+            st = fn(h, kp, vp, n, ws.data_ptr(), wsb, sp)
+        else:
+            st = fn(h, kp, n, ws.data_ptr(), wsb, sp)
+        if st != 0:
+            raise RuntimeError(dts.status_string(st))
+
+    def restore():
+        k.copy_(pk)
+        if has_v:
+            v.copy_(pv)
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            import torch.distributed as tdist
+            tdist.barrier()
+
+    for _ in range(args.warmup):
+        restore()
+        sort_once(k.data_ptr(), v.data_ptr() if has_v else None)
+    st = dts.dtsort_last_device_error(h, sp)
+    if st != 0:
+        raise RuntimeError("device: " + dts.status_string(st))
+    # ---- timed: K sorts, CUDA events around each sort on its stream ----
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    barrier()
+    with ClockSampler(local) as clk:
+        for i in range(args.steps):
+            restore()
+            ev[i][0].record(stream)
+            sort_once(k.data_ptr(), v.data_ptr() if has_v else None)
+            ev[i][1].record(stream)
+        barrier()
+    st = dts.dtsort_last_device_error(h, sp)
+    if st != 0:
+        raise RuntimeError("device: " + dts.status_string(st))
+    ms = [a.elapsed_time(b) for a, b in ev]
+    ms_step = sum(ms) / len(ms)
+    if world > 1:
+        import torch.distributed as tdist
+        t = torch.tensor([ms_step], device=dev)
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        ms_step = float(t.item())
+    stats = dts.dtsort_get_stats(h).as_dict()
+    # ---- end to end: host buffers in, sorted host buffers out ----
+    e2e = None
+    if not args.no_e2e:
+        ok_k = torch.empty_like(hk, pin_memory=True)
+        ok_v = torch.empty_like(hv, pin_memory=True) if has_v else None
+        e_ms = []
+        for i in range(max(1, min(args.steps, 3))):
+            barrier()
+            t0 = torch.cuda.Event(enable_timing=True)
+            t1 = torch.cuda.Event(enable_timing=True)
+            t0.record(stream)
+            k.copy_(hk, non_blocking=True)
+            if has_v:
+                v.copy_(hv, non_blocking=True)
+            sort_once(k.data_ptr(), v.data_ptr() if has_v else None)
+            ok_k.copy_(k, non_blocking=True)
+            if has_v:
+                ok_v.copy_(v, non_blocking=True)
+            t1.record(stream)
+            barrier()
+            e_ms.append(t0.elapsed_time(t1))
+        e_ms_step = sum(e_ms) / len(e_ms)
+        by = n * (kbytes * (2 if has_v else 1))
+        e2e = {"value": world * n / (e_ms_step / 1e3), "unit": "keys/s",
+               "h2d_bytes_per_step": by, "d2h_bytes_per_step": by,
+               "ms_per_step": e_ms_step}
+    if rank != 0:
+        return 0
+    peak, peak_kind = peaks()
+    b_alg = B_ALG[args.op] * n
+    achieved = b_alg / (ms_step / 1e3) / 1e9
+    line = {
+        "metric": METRIC, "value": world * n / (ms_step / 1e3), "unit": "keys/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": args.op, "data": "synthetic",
+        "config": {"workload": "stable sort, %s, n=%d, keys %s seed %d, values = index"
+                               % (args.op, n, args.dist, args.seed),
+                   "n": n, "dist": args.dist, "l2": "inputs 8+ GB per step >> L2",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "peak_kind": peak_kind, "bytes_per_record": B_ALG[args.op],
+                     "kernel": "dts::dtsort_kernel (one persistent launch per sort)"},
+        "gpu_launches": args.steps,
+        "clocks": clk.summary(),
+        "e2e": e2e,
+        "stats": {"levels": stats["levels"], "phase_ms": stats["phase_ms"],
+                  "heavy_keys": stats["heavy_keys"][:4],
+                  "finisher_tasks": stats["finisher_tasks"],
+                  "merge_records": stats["merge_records"]},
+        "ms_steps": ms,
+    }
+    if not args.no_cpu_baseline and world == 1:
+        sample = min(args.cpu_sample, n)
+        val, cores, dt = cpu_oracle_time(args, sample)
+        line["cpu_baseline"] = {"value": val, "unit": "keys/s", "cores": cores,
+                                "kind": "oracle",
+                                "sample": "first %d records of the same seeded stream "
+                                          "(%.1f s)" % (sample, dt)}
+    print(json.dumps(line), flush=True)
+    dts.dtsort_destroy(h)
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

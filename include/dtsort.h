@@ -1,0 +1,222 @@
+/*
+ * dtsort -- stable MSD integer sort with heavy-key detection and dovetail
+ * merging, for NVIDIA GB300 (sm_103a).
+ *
+ * The operation (Sec. 2.3 of "Parallel Integer Sort: Theory and Practice",
+ * Dong, Dhulipala, Gu, Sun, PPoPP'24): n records with unsigned integer keys
+ * in [0, 2^w) are reordered into non-decreasing key order, STABLY (records
+ * with equal keys keep their input order).  The result is written back into
+ * the input arrays ("in place" refers to the interface; O(n) extra space is
+ * used, passed in as a caller-owned workspace).  The method is DovetailSort
+ * (Alg. 2): per subproblem, sample the keys and detect heavy (highly
+ * duplicated) keys, distribute records into light buckets (one per MSD zone)
+ * and heavy buckets (one per heavy key) with a stable counting sort, recurse
+ * on light buckets only, and merge each zone's light and heavy runs (Alg. 3,
+ * DTMerge).  A stable sort's output is unique, so every parameter below
+ * (digit width, tile size, sample size, on-chip capacity, learned bucketing)
+ * changes speed only, never the output.
+ *
+ * Conventions for every call:
+ *   - Pointers named keys/values/offsets/workspace are DEVICE pointers on the
+ *     handle's device.  The caller owns them; the library never frees them or
+ *     keeps them after the call has been enqueued.  Keys and values are two
+ *     separate arrays (structure of arrays); values == NULL means key-only.
+ *     Values are opaque payload of the key's width, copied bit for bit.
+ *   - Keys compare as unsigned integers.
+ *   - Calls are asynchronous and stream-ordered on `stream` (a cudaStream_t;
+ *     NULL is the legacy default stream).  The return value reports only what
+ *     the host can check before launching.  Errors found on the device (a
+ *     bounded wait that timed out, an exhausted internal table) are latched
+ *     in the handle and read with dtsort_last_device_error().
+ *   - No call allocates device memory, except dtsort_create() (a few KB).
+ *   - n == 0 is a no-op returning DTSORT_OK.  n < 0, or a NULL pointer where
+ *     n > 0 needs one, returns DTSORT_ERR_INVALID_ARG.  A workspace smaller
+ *     than dtsort_workspace_bytes() returns DTSORT_ERR_WORKSPACE_TOO_SMALL.
+ *     Keys/values must be aligned to their own width; the workspace to 256 B.
+ *   - A handle is used by one host thread at a time.  Two sorts that use the
+ *     same workspace must not overlap on the GPU.
+ */
+#ifndef DTSORT_H_
+#define DTSORT_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define DTSORT_API __attribute__((visibility("default")))
+#else
+#define DTSORT_API
+#endif
+
+/* Same type as cudaStream_t; declared here so that no CUDA header is needed. */
+typedef struct CUstream_st *dtsort_stream;
+
+typedef enum {
+  DTSORT_OK = 0,
+  DTSORT_ERR_INVALID_ARG = 1,
+  DTSORT_ERR_WORKSPACE_TOO_SMALL = 2,
+  DTSORT_ERR_CUDA = 3,             /* a CUDA runtime call failed */
+  DTSORT_ERR_DEVICE_TIMEOUT = 4,   /* a bounded device-side wait expired */
+  DTSORT_ERR_UNSUPPORTED = 5,      /* e.g. no sm_103a device */
+  DTSORT_ERR_INTERNAL = 6          /* an internal device table overflowed */
+} dtsort_status;
+
+typedef enum {
+  DTSORT_OP_U32 = 0,     /* 32-bit keys, key-only */
+  DTSORT_OP_U32_KV = 1,  /* 32-bit keys, 32-bit values */
+  DTSORT_OP_U64 = 2,     /* 64-bit keys, key-only */
+  DTSORT_OP_U64_KV = 3   /* 64-bit keys, 64-bit values */
+} dtsort_op;
+
+typedef enum {
+  DTSORT_BUCKETING_DIGIT = 0,   /* MSD zones = the next gamma key bits (Alg. 2) */
+  DTSORT_BUCKETING_LEARNED = 1  /* zones from a CDF model fit on the sample */
+} dtsort_bucketing;
+
+typedef struct dtsort_handle_s *dtsort_handle;
+
+/* Tuning knobs.  Zero fields mean "default" (or "autotuned" where autotune is
+ * on).  None of them changes the output. */
+typedef struct {
+  int32_t gamma_max;         /* largest digit width per level, 1..9 (default 9) */
+  int32_t finisher_capacity; /* largest bucket the on-chip base case sorts,
+                                in records (default: what fits on chip) */
+  int32_t heavy_detection;   /* 1 on (default), -1 off (the paper's "Plain") */
+  int32_t bucketing;         /* dtsort_bucketing (default DIGIT) */
+  uint64_t seed;             /* sampler seed (default 1) */
+  int32_t sample_log_factor; /* samples per level = 2^gamma * ceil(log2 n),
+                                capped on chip; 0 = default */
+  int32_t autotune;          /* 1: use the on-disk autotune cache (default 0) */
+  int32_t learned_segments;  /* learned bucketing: knots of the CDF table
+                                (default 1024) */
+  int32_t learned_train_steps; /* learned bucketing: Adam steps (default 200) */
+  int32_t wait_limit_ms;     /* bound of every device-side wait (default 2000);
+                                when it expires the sort latches
+                                DTSORT_ERR_DEVICE_TIMEOUT and writes nothing more */
+  int32_t debug_fault;       /* testing only: 1 = the second tile of the first
+                                distribution never publishes its look-back
+                                status, so its successors' waits expire */
+  int32_t reserved[6];
+} dtsort_options;
+
+/* Statistics of the last completed sort on this handle (read after sync). */
+typedef struct {
+  int32_t levels;                 /* distribution levels executed */
+  int32_t status;                 /* latched device status (dtsort_status) */
+  int64_t segments[16];           /* subproblems distributed at level l */
+  int64_t records[16];            /* records distributed at level l */
+  int64_t heavy_keys[16];         /* heavy keys detected at level l */
+  int64_t heavy_records[16];      /* records placed in heavy buckets at level l */
+  int64_t overflow_records[16];   /* records in overflow buckets at level l */
+  int64_t finisher_tasks;         /* buckets sorted by the on-chip base case */
+  int64_t finisher_records;
+  int64_t copy_records;           /* records moved by plain copies */
+  int64_t merge_zones;            /* MSD zones that needed a dovetail merge */
+  int64_t merge_records;          /* records written by dovetail merges */
+  int64_t learned_fixup_records;  /* learned bucketing: records whose predicted
+                                     bucket needed the exact fix-up */
+  int64_t learned_fixup_steps;
+  double learned_bucket_cv;       /* learned bucketing: coefficient of
+                                     variation of the level-0 bucket sizes */
+  double learned_bucket_max_over_mean;
+  double phase_ms[8];             /* device time per phase kind: 0 setup,
+                                     1 sample, 2 histogram, 3 scan, 4 scatter,
+                                     5 finisher, 6 merge, 7 total */
+  int64_t reserved[8];
+} dtsort_stats;
+
+DTSORT_API const char *dtsort_status_string(dtsort_status s);
+
+/* Creates a handle on CUDA device `device`.  Allocates its small state
+ * (status word, statistics, timing) on that device.  Fails with
+ * DTSORT_ERR_UNSUPPORTED when the device is not compute capability 10.3. */
+DTSORT_API dtsort_status dtsort_create(dtsort_handle *out, int device);
+DTSORT_API dtsort_status dtsort_destroy(dtsort_handle h);
+
+/* Fills *opt with the defaults. */
+DTSORT_API dtsort_status dtsort_default_options(dtsort_options *opt);
+/* opt == NULL restores the defaults.  Invalid values -> INVALID_ARG. */
+DTSORT_API dtsort_status dtsort_set_options(dtsort_handle h, const dtsort_options *opt);
+DTSORT_API dtsort_status dtsort_get_options(dtsort_handle h, dtsort_options *opt);
+
+/* Workspace size in bytes for sorting n records (num_segments arrays for the
+ * segmented calls, 1 otherwise) with the handle's current options.  The
+ * workspace holds the second (ping-pong) copy of keys and values and the
+ * per-level tables; it is about n * (key + value bytes) * 1.1 + 4 MB. */
+DTSORT_API dtsort_status dtsort_workspace_bytes(dtsort_handle h, dtsort_op op, int64_t n,
+                                     int64_t num_segments, size_t *bytes);
+
+/* Stable sort of keys[0..n) (and values[0..n) alongside) in place. */
+DTSORT_API dtsort_status dtsort_u32(dtsort_handle h, uint32_t *keys, int64_t n,
+                         void *workspace, size_t workspace_bytes,
+                         dtsort_stream stream);
+DTSORT_API dtsort_status dtsort_u32_kv(dtsort_handle h, uint32_t *keys, uint32_t *values,
+                            int64_t n, void *workspace, size_t workspace_bytes,
+                            dtsort_stream stream);
+DTSORT_API dtsort_status dtsort_u64(dtsort_handle h, uint64_t *keys, int64_t n,
+                         void *workspace, size_t workspace_bytes,
+                         dtsort_stream stream);
+DTSORT_API dtsort_status dtsort_u64_kv(dtsort_handle h, uint64_t *keys, uint64_t *values,
+                            int64_t n, void *workspace, size_t workspace_bytes,
+                            dtsort_stream stream);
+
+/* Segmented (batched) stable sort: every array s = [offsets[s], offsets[s+1])
+ * of keys/values is sorted on its own, all in one persistent kernel launch.
+ * offsets: DEVICE int64[num_segments + 1], offsets[0] == 0, non-decreasing,
+ * offsets[num_segments] == n (not checked on the host; a violation is
+ * reported as DTSORT_ERR_INVALID_ARG by dtsort_last_device_error()).  Empty
+ * arrays are allowed.  The launch sequence contains no host synchronisation,
+ * so it can be captured into a CUDA graph once the sizes are fixed. */
+DTSORT_API dtsort_status dtsort_segmented_u32(dtsort_handle h, uint32_t *keys,
+                                   const int64_t *offsets, int64_t num_segments,
+                                   int64_t n, void *workspace,
+                                   size_t workspace_bytes, dtsort_stream stream);
+DTSORT_API dtsort_status dtsort_segmented_u32_kv(dtsort_handle h, uint32_t *keys,
+                                      uint32_t *values, const int64_t *offsets,
+                                      int64_t num_segments, int64_t n,
+                                      void *workspace, size_t workspace_bytes,
+                                      dtsort_stream stream);
+DTSORT_API dtsort_status dtsort_segmented_u64(dtsort_handle h, uint64_t *keys,
+                                   const int64_t *offsets, int64_t num_segments,
+                                   int64_t n, void *workspace,
+                                   size_t workspace_bytes, dtsort_stream stream);
+DTSORT_API dtsort_status dtsort_segmented_u64_kv(dtsort_handle h, uint64_t *keys,
+                                      uint64_t *values, const int64_t *offsets,
+                                      int64_t num_segments, int64_t n,
+                                      void *workspace, size_t workspace_bytes,
+                                      dtsort_stream stream);
+
+/* Synchronises `stream` and returns the device status latched by the sorts
+ * enqueued on this handle since the previous call (then clears it). */
+DTSORT_API dtsort_status dtsort_last_device_error(dtsort_handle h, dtsort_stream stream);
+
+/* Copies the statistics of the most recent sort (synchronises the device). */
+DTSORT_API dtsort_status dtsort_get_stats(dtsort_handle h, dtsort_stats *out);
+
+/* ---- diagnostics: single steps of the method, for testing ---------------- */
+
+/* Alg. 2 step 1 on one subproblem keys[start .. start+size) of an array whose
+ * original length is n_total: draws `count` sample keys at positions
+ * start + (SplitMix64 output i mod size), where output i comes from the
+ * SplitMix64 sequence (Steele, Lea, Flood 2014) started from
+ *   seed ^ start ^ (size * 0x9E3779B97F4A7C15) ^ (hi << 57),
+ * sorts them, keeps every L-th (S[L-1], S[2L-1], ...), and reports the keys
+ * seen at least twice there (heavy keys, increasing) and the largest sample.
+ * heavy_out: DEVICE uint64[count / 2 + 1]; nheavy_out, max_out: DEVICE.
+ * count <= 8192.  key_bytes is 4 or 8. */
+DTSORT_API dtsort_status dtsort_debug_sample(dtsort_handle h, const void *keys,
+                                  int key_bytes, int64_t start, int64_t size,
+                                  int hi, uint64_t seed, int64_t count,
+                                  int64_t L, uint64_t *heavy_out,
+                                  int64_t *nheavy_out, uint64_t *max_out,
+                                  dtsort_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DTSORT_H_ */

@@ -1,0 +1,413 @@
+// C-ABI of dtsort (include/dtsort.h): argument checks, workspace layout and
+// the one cooperative launch per sort call.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <cstring>
+#include <new>
+
+#include "../../include/dtsort.h"
+#include "dtsort_launch.h"
+
+namespace {
+
+using dts::DevStats;
+using dts::KernelShape;
+using dts::Params;
+
+constexpr int kOps = 4;
+
+struct Layout {
+  size_t tkeys, tvals, ctl, segs0, segs1, info, bcount, bstart, lid, heavy, hashk, hashid,
+      status, tasks, zones, mhk, mhs, mhst, total;
+  int64_t maxseg, bmax, hmax, zmax, hashmax, swords, tmax, mhmax;
+  int cap;
+  int64_t target;
+};
+
+struct Opts {
+  int gamma_max, cap, heavy_on, sample_factor, debug_fault;
+  uint64_t seed;
+  unsigned long long wait_ns;
+};
+
+}  // namespace
+
+struct dtsort_handle_s {
+  int device = 0;
+  int nsm = 0;
+  dtsort_options opt{};
+  int *d_status = nullptr;
+  DevStats *d_stats = nullptr;
+  KernelShape shape[kOps]{};
+  bool shape_ok[kOps]{};
+};
+
+namespace {
+
+int key_bytes(int op) { return (op == DTSORT_OP_U32 || op == DTSORT_OP_U32_KV) ? 4 : 8; }
+bool has_vals(int op) { return op == DTSORT_OP_U32_KV || op == DTSORT_OP_U64_KV; }
+
+cudaError_t get_shape(dtsort_handle h, int op, KernelShape **out) {
+  if (!h->shape_ok[op]) {
+    cudaError_t e;
+    switch (op) {
+      case DTSORT_OP_U32: e = dts::shape_u32(&h->shape[op]); break;
+      case DTSORT_OP_U32_KV: e = dts::shape_u32kv(&h->shape[op]); break;
+      case DTSORT_OP_U64: e = dts::shape_u64(&h->shape[op]); break;
+      default: e = dts::shape_u64kv(&h->shape[op]); break;
+    }
+    if (e != cudaSuccess) return e;
+    h->shape_ok[op] = true;
+  }
+  *out = &h->shape[op];
+  return cudaSuccess;
+}
+
+Opts effective(const dtsort_options &o, const KernelShape &ks) {
+  Opts r;
+  r.gamma_max = o.gamma_max > 0 ? o.gamma_max : dts::GAMMA_HW;
+  r.cap = (o.finisher_capacity > 0 && o.finisher_capacity < ks.fin_cap) ? o.finisher_capacity
+                                                                        : ks.fin_cap;
+  r.heavy_on = o.heavy_detection >= 0 ? 1 : 0;
+  r.sample_factor = o.sample_log_factor > 0 ? o.sample_log_factor : 1;
+  r.seed = o.seed ? o.seed : 1;
+  r.debug_fault = o.debug_fault;
+  r.wait_ns = (unsigned long long)(o.wait_limit_ms > 0 ? o.wait_limit_ms : 2000) * 1000000ull;
+  return r;
+}
+
+size_t up(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Upper bounds of every device table for n records in nsegs arrays.  The
+// digit width rule gives 2^gamma < 2*size/target for every subproblem
+// (size > cap > target), which bounds the per-level sums below.
+Layout make_layout(int kb, int vb, int64_t n, int64_t nsegs, const Opts &o, int tile) {
+  Layout L{};
+  L.cap = o.cap;
+  L.target = std::max<int64_t>(16, (int64_t)o.cap * 7 / 10);
+  const int64_t nt = n / L.target + 1;
+  L.maxseg = n / (o.cap + 1) + 2;
+  L.bmax = 3 * nt + L.maxseg + 1024;
+  L.hmax = nt + L.maxseg + 1024;
+  L.zmax = 2 * nt + 2 * L.maxseg + 1024;
+  L.hashmax = 2 * nt + L.maxseg + 1024;
+  L.swords = (int64_t)dts::NB_HW * (n / tile + 1) + L.bmax;
+  L.tmax = 2 * L.bmax + 2 * (n / dts::COPY_CHUNK + 1) + nsegs + 4096;
+  L.mhmax = 4 * L.hmax + 4096;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t r = off;
+    off = up(off + bytes);
+    return r;
+  };
+  L.tkeys = take((size_t)n * kb);
+  L.tvals = take((size_t)n * vb);
+  L.ctl = take(sizeof(dts::Ctl));
+  L.segs0 = take(sizeof(dts::Seg) * (size_t)L.maxseg);
+  L.segs1 = take(sizeof(dts::Seg) * (size_t)L.maxseg);
+  L.info = take(sizeof(dts::SegInfo) * (size_t)L.maxseg);
+  L.bcount = take(8 * (size_t)L.bmax);
+  L.bstart = take(8 * (size_t)L.bmax);
+  L.lid = take(4 * (size_t)L.zmax);
+  L.heavy = take((size_t)kb * L.hmax);
+  L.hashk = take((size_t)kb * L.hashmax);
+  L.hashid = take(2 * (size_t)L.hashmax);
+  L.status = take(8 * (size_t)L.swords);
+  L.tasks = take(sizeof(dts::Task) * (size_t)L.tmax);
+  L.zones = take(sizeof(dts::MZone) * (size_t)L.mhmax);
+  L.mhk = take((size_t)kb * L.mhmax);
+  L.mhs = take(8 * (size_t)L.mhmax);
+  L.mhst = take(8 * (size_t)L.mhmax);
+  L.total = off;
+  return L;
+}
+
+dtsort_status from_cuda(cudaError_t e) {
+  return e == cudaSuccess ? DTSORT_OK : DTSORT_ERR_CUDA;
+}
+
+dtsort_status run_sort(dtsort_handle h, int op, void *keys, void *vals, const int64_t *offsets,
+                       int64_t nsegs, int64_t n, void *ws, size_t ws_bytes, cudaStream_t s) {
+  if (!h) return DTSORT_ERR_INVALID_ARG;
+  if (n < 0 || nsegs < 0) return DTSORT_ERR_INVALID_ARG;
+  if (offsets && nsegs == 0) return n == 0 ? DTSORT_OK : DTSORT_ERR_INVALID_ARG;
+  if (n == 0) return DTSORT_OK;
+  if (!keys || (has_vals(op) && !vals) || !ws) return DTSORT_ERR_INVALID_ARG;
+  const int kb = key_bytes(op), vb = has_vals(op) ? kb : 0;
+  if (((uintptr_t)keys % kb) || (vals && ((uintptr_t)vals % kb)) || ((uintptr_t)ws % 256))
+    return DTSORT_ERR_INVALID_ARG;
+  int cur = -1;
+  if (cudaGetDevice(&cur) != cudaSuccess) return DTSORT_ERR_CUDA;
+  if (cur != h->device && cudaSetDevice(h->device) != cudaSuccess) return DTSORT_ERR_CUDA;
+  KernelShape *ks = nullptr;
+  cudaError_t e = get_shape(h, op, &ks);
+  if (e != cudaSuccess) return DTSORT_ERR_CUDA;
+  if (ks->blocks_per_sm < 1) return DTSORT_ERR_UNSUPPORTED;
+  const Opts o = effective(h->opt, *ks);
+  const Layout L = make_layout(kb, vb, n, offsets ? nsegs : 1, o, ks->tile);
+  if (ws_bytes < L.total) return DTSORT_ERR_WORKSPACE_TOO_SMALL;
+  char *w = (char *)ws;
+  Params P{};
+  P.keys[0] = keys;
+  P.keys[1] = w + L.tkeys;
+  P.vals[0] = vb ? vals : nullptr;
+  P.vals[1] = vb ? (void *)(w + L.tvals) : nullptr;
+  P.n = n;
+  P.offsets = offsets;
+  P.nsegs_in = offsets ? nsegs : 1;
+  P.key_bits = 8 * kb;
+  P.gamma_max = std::min(o.gamma_max, dts::GAMMA_HW);
+  P.cap = L.cap;
+  P.heavy_on = o.heavy_on;
+  P.target = L.target;
+  P.seed = o.seed;
+  P.sample_factor = o.sample_factor;
+  P.debug_fault = o.debug_fault;
+  P.wait_ns = o.wait_ns;
+  P.ctl = (dts::Ctl *)(w + L.ctl);
+  P.segs[0] = (dts::Seg *)(w + L.segs0);
+  P.segs[1] = (dts::Seg *)(w + L.segs1);
+  P.info = (dts::SegInfo *)(w + L.info);
+  P.bcount = (int64_t *)(w + L.bcount);
+  P.bstart = (int64_t *)(w + L.bstart);
+  P.lid = (int32_t *)(w + L.lid);
+  P.heavy = w + L.heavy;
+  P.hash_keys = w + L.hashk;
+  P.hash_ids = (uint16_t *)(w + L.hashid);
+  P.status = (unsigned long long *)(w + L.status);
+  P.tasks = (dts::Task *)(w + L.tasks);
+  P.zones = (dts::MZone *)(w + L.zones);
+  P.mh_keys = w + L.mhk;
+  P.mh_sizes = (int64_t *)(w + L.mhs);
+  P.mh_start = (int64_t *)(w + L.mhst);
+  P.maxseg = L.maxseg;
+  P.bmax = L.bmax;
+  P.hmax = L.hmax;
+  P.zmax = L.zmax;
+  P.hashmax = L.hashmax;
+  P.swords = L.swords;
+  P.tmax = L.tmax;
+  P.mhmax = L.mhmax;
+  P.dev_status = h->d_status;
+  P.stats = h->d_stats;
+  e = cudaMemsetAsync(P.ctl, 0, sizeof(dts::Ctl), s);
+  if (e != cudaSuccess) return DTSORT_ERR_CUDA;
+  const int grid = h->nsm * std::min(ks->blocks_per_sm, 2);
+  switch (op) {
+    case DTSORT_OP_U32: e = dts::launch_u32(P, grid, s); break;
+    case DTSORT_OP_U32_KV: e = dts::launch_u32kv(P, grid, s); break;
+    case DTSORT_OP_U64: e = dts::launch_u64(P, grid, s); break;
+    default: e = dts::launch_u64kv(P, grid, s); break;
+  }
+  return from_cuda(e);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *dtsort_status_string(dtsort_status s) {
+  switch (s) {
+    case DTSORT_OK: return "DTSORT_OK";
+    case DTSORT_ERR_INVALID_ARG: return "DTSORT_ERR_INVALID_ARG: invalid argument";
+    case DTSORT_ERR_WORKSPACE_TOO_SMALL: return "DTSORT_ERR_WORKSPACE_TOO_SMALL";
+    case DTSORT_ERR_CUDA: return "DTSORT_ERR_CUDA: a CUDA runtime call failed";
+    case DTSORT_ERR_DEVICE_TIMEOUT: return "DTSORT_ERR_DEVICE_TIMEOUT: a bounded device wait expired";
+    case DTSORT_ERR_UNSUPPORTED: return "DTSORT_ERR_UNSUPPORTED: needs a compute capability 10.3 GPU";
+    case DTSORT_ERR_INTERNAL: return "DTSORT_ERR_INTERNAL: an internal device table overflowed";
+  }
+  return "unknown dtsort status";
+}
+
+dtsort_status dtsort_default_options(dtsort_options *opt) {
+  if (!opt) return DTSORT_ERR_INVALID_ARG;
+  std::memset(opt, 0, sizeof(*opt));
+  opt->gamma_max = dts::GAMMA_HW;
+  opt->heavy_detection = 1;
+  opt->bucketing = DTSORT_BUCKETING_DIGIT;
+  opt->seed = 1;
+  opt->sample_log_factor = 1;
+  opt->learned_segments = 1024;
+  opt->learned_train_steps = 200;
+  opt->wait_limit_ms = 2000;
+  return DTSORT_OK;
+}
+
+dtsort_status dtsort_create(dtsort_handle *out, int device) {
+  if (!out) return DTSORT_ERR_INVALID_ARG;
+  *out = nullptr;
+  int count = 0;
+  if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count)
+    return count == 0 ? DTSORT_ERR_UNSUPPORTED : DTSORT_ERR_INVALID_ARG;
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) return DTSORT_ERR_CUDA;
+  if (prop.major != 10 || prop.minor != 3) return DTSORT_ERR_UNSUPPORTED;
+  if (!prop.cooperativeLaunch) return DTSORT_ERR_UNSUPPORTED;
+  int cur = -1;
+  if (cudaGetDevice(&cur) != cudaSuccess) return DTSORT_ERR_CUDA;
+  if (cudaSetDevice(device) != cudaSuccess) return DTSORT_ERR_CUDA;
+  dtsort_handle h = new (std::nothrow) dtsort_handle_s();
+  if (!h) return DTSORT_ERR_INTERNAL;
+  h->device = device;
+  h->nsm = prop.multiProcessorCount;
+  dtsort_default_options(&h->opt);
+  dtsort_status st = DTSORT_OK;
+  if (cudaMalloc(&h->d_status, sizeof(int)) != cudaSuccess ||
+      cudaMalloc(&h->d_stats, sizeof(DevStats)) != cudaSuccess ||
+      cudaMemset(h->d_status, 0, sizeof(int)) != cudaSuccess ||
+      cudaMemset(h->d_stats, 0, sizeof(DevStats)) != cudaSuccess) {
+    st = DTSORT_ERR_CUDA;
+  }
+  if (cur >= 0) cudaSetDevice(cur);
+  if (st != DTSORT_OK) {
+    cudaFree(h->d_status);
+    cudaFree(h->d_stats);
+    delete h;
+    return st;
+  }
+  *out = h;
+  return DTSORT_OK;
+}
+
+dtsort_status dtsort_destroy(dtsort_handle h) {
+  if (!h) return DTSORT_ERR_INVALID_ARG;
+  cudaFree(h->d_status);
+  cudaFree(h->d_stats);
+  delete h;
+  return DTSORT_OK;
+}
+
+dtsort_status dtsort_set_options(dtsort_handle h, const dtsort_options *opt) {
+  if (!h) return DTSORT_ERR_INVALID_ARG;
+  if (!opt) return dtsort_default_options(&h->opt);
+  if (opt->gamma_max < 0 || opt->gamma_max > dts::GAMMA_HW || opt->finisher_capacity < 0 ||
+      opt->sample_log_factor < 0 || opt->sample_log_factor > 64 ||
+      (opt->bucketing != DTSORT_BUCKETING_DIGIT && opt->bucketing != DTSORT_BUCKETING_LEARNED) ||
+      opt->learned_segments < 0 || opt->learned_train_steps < 0 || opt->wait_limit_ms < 0 ||
+      opt->debug_fault < 0 || opt->debug_fault > 1)
+    return DTSORT_ERR_INVALID_ARG;
+  h->opt = *opt;
+  return DTSORT_OK;
+}
+
+dtsort_status dtsort_get_options(dtsort_handle h, dtsort_options *opt) {
+  if (!h || !opt) return DTSORT_ERR_INVALID_ARG;
+  *opt = h->opt;
+  return DTSORT_OK;
+}
+
+dtsort_status dtsort_workspace_bytes(dtsort_handle h, dtsort_op op, int64_t n,
+                                     int64_t num_segments, size_t *bytes) {
+  if (!h || !bytes || n < 0 || num_segments < 0 || (int)op < 0 || (int)op >= kOps)
+    return DTSORT_ERR_INVALID_ARG;
+  int cur = -1;
+  if (cudaGetDevice(&cur) != cudaSuccess) return DTSORT_ERR_CUDA;
+  if (cur != h->device && cudaSetDevice(h->device) != cudaSuccess) return DTSORT_ERR_CUDA;
+  KernelShape *ks = nullptr;
+  if (get_shape(h, op, &ks) != cudaSuccess) return DTSORT_ERR_CUDA;
+  const Opts o = effective(h->opt, *ks);
+  const int kb = key_bytes(op), vb = has_vals(op) ? kb : 0;
+  *bytes = make_layout(kb, vb, n, num_segments > 0 ? num_segments : 1, o, ks->tile).total;
+  return DTSORT_OK;
+}
+
+dtsort_status dtsort_u32(dtsort_handle h, uint32_t *keys, int64_t n, void *ws, size_t wsb,
+                         dtsort_stream s) {
+  return run_sort(h, DTSORT_OP_U32, keys, nullptr, nullptr, 1, n, ws, wsb, (cudaStream_t)s);
+}
+dtsort_status dtsort_u32_kv(dtsort_handle h, uint32_t *keys, uint32_t *values, int64_t n,
+                            void *ws, size_t wsb, dtsort_stream s) {
+  return run_sort(h, DTSORT_OP_U32_KV, keys, values, nullptr, 1, n, ws, wsb, (cudaStream_t)s);
+}
+dtsort_status dtsort_u64(dtsort_handle h, uint64_t *keys, int64_t n, void *ws, size_t wsb,
+                         dtsort_stream s) {
+  return run_sort(h, DTSORT_OP_U64, keys, nullptr, nullptr, 1, n, ws, wsb, (cudaStream_t)s);
+}
+dtsort_status dtsort_u64_kv(dtsort_handle h, uint64_t *keys, uint64_t *values, int64_t n,
+                            void *ws, size_t wsb, dtsort_stream s) {
+  return run_sort(h, DTSORT_OP_U64_KV, keys, values, nullptr, 1, n, ws, wsb, (cudaStream_t)s);
+}
+
+dtsort_status dtsort_segmented_u32(dtsort_handle h, uint32_t *keys, const int64_t *off,
+                                   int64_t ns, int64_t n, void *ws, size_t wsb,
+                                   dtsort_stream s) {
+  if (!off && n > 0) return DTSORT_ERR_INVALID_ARG;
+  return run_sort(h, DTSORT_OP_U32, keys, nullptr, off, ns, n, ws, wsb, (cudaStream_t)s);
+}
+dtsort_status dtsort_segmented_u32_kv(dtsort_handle h, uint32_t *keys, uint32_t *values,
+                                      const int64_t *off, int64_t ns, int64_t n, void *ws,
+                                      size_t wsb, dtsort_stream s) {
+  if (!off && n > 0) return DTSORT_ERR_INVALID_ARG;
+  return run_sort(h, DTSORT_OP_U32_KV, keys, values, off, ns, n, ws, wsb, (cudaStream_t)s);
+}
+dtsort_status dtsort_segmented_u64(dtsort_handle h, uint64_t *keys, const int64_t *off,
+                                   int64_t ns, int64_t n, void *ws, size_t wsb,
+                                   dtsort_stream s) {
+  if (!off && n > 0) return DTSORT_ERR_INVALID_ARG;
+  return run_sort(h, DTSORT_OP_U64, keys, nullptr, off, ns, n, ws, wsb, (cudaStream_t)s);
+}
+dtsort_status dtsort_segmented_u64_kv(dtsort_handle h, uint64_t *keys, uint64_t *values,
+                                      const int64_t *off, int64_t ns, int64_t n, void *ws,
+                                      size_t wsb, dtsort_stream s) {
+  if (!off && n > 0) return DTSORT_ERR_INVALID_ARG;
+  return run_sort(h, DTSORT_OP_U64_KV, keys, values, off, ns, n, ws, wsb, (cudaStream_t)s);
+}
+
+dtsort_status dtsort_last_device_error(dtsort_handle h, dtsort_stream s) {
+  if (!h) return DTSORT_ERR_INVALID_ARG;
+  if (cudaStreamSynchronize((cudaStream_t)s) != cudaSuccess) return DTSORT_ERR_CUDA;
+  int v = 0;
+  if (cudaMemcpy(&v, h->d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return DTSORT_ERR_CUDA;
+  if (v && cudaMemset(h->d_status, 0, sizeof(int)) != cudaSuccess) return DTSORT_ERR_CUDA;
+  return (dtsort_status)v;
+}
+
+dtsort_status dtsort_get_stats(dtsort_handle h, dtsort_stats *out) {
+  if (!h || !out) return DTSORT_ERR_INVALID_ARG;
+  DevStats d;
+  if (cudaDeviceSynchronize() != cudaSuccess) return DTSORT_ERR_CUDA;
+  if (cudaMemcpy(&d, h->d_stats, sizeof(d), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return DTSORT_ERR_CUDA;
+  std::memset(out, 0, sizeof(*out));
+  out->levels = d.levels;
+  out->status = d.status;
+  for (int l = 0; l < 16; ++l) {
+    out->segments[l] = d.segments[l];
+    out->records[l] = d.records[l];
+    out->heavy_keys[l] = d.heavy_keys[l];
+    out->heavy_records[l] = d.heavy_records[l];
+    out->overflow_records[l] = d.overflow_records[l];
+  }
+  out->finisher_tasks = d.finisher_tasks;
+  out->finisher_records = d.finisher_records;
+  out->copy_records = d.copy_records;
+  out->merge_zones = d.merge_zones;
+  out->merge_records = d.merge_records;
+  out->learned_fixup_records = d.learned_fixup_records;
+  out->learned_fixup_steps = d.learned_fixup_steps;
+  out->learned_bucket_cv = d.learned_cv;
+  out->learned_bucket_max_over_mean = d.learned_mom;
+  for (int k = 0; k < 8; ++k) out->phase_ms[k] = d.phase_ms[k];
+  return DTSORT_OK;
+}
+
+dtsort_status dtsort_debug_sample(dtsort_handle h, const void *keys, int key_bytes_,
+                                  int64_t start, int64_t size, int hi, uint64_t seed,
+                                  int64_t count, int64_t L, uint64_t *heavy_out,
+                                  int64_t *nheavy_out, uint64_t *max_out, dtsort_stream s) {
+  if (!h || !keys || !heavy_out || !nheavy_out || !max_out) return DTSORT_ERR_INVALID_ARG;
+  if ((key_bytes_ != 4 && key_bytes_ != 8) || start < 0 || size <= 0 || count <= 0 ||
+      count > dts::SMAX || L <= 0 || hi < 0 || hi > 8 * key_bytes_)
+    return DTSORT_ERR_INVALID_ARG;
+  cudaError_t e = key_bytes_ == 4
+                      ? dts::launch_sample_u32(keys, start, size, hi, seed, count, L, heavy_out,
+                                               nheavy_out, max_out, (cudaStream_t)s)
+                      : dts::launch_sample_u64(keys, start, size, hi, seed, count, L, heavy_out,
+                                               nheavy_out, max_out, (cudaStream_t)s);
+  return from_cuda(e);
+}
+
+}  // extern "C"

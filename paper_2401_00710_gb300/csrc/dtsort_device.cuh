@@ -1,0 +1,378 @@
+// Device side of dtsort: the stable MSD distribution of DovetailSort (Alg. 2)
+// for sm_103a, organised as phases of one persistent cooperative kernel.
+//
+// One level of the recursion (all subproblems of that level together):
+//   setup    (1 CTA)   digit width per subproblem, arena reservations, tiles
+//   sample   (CTA/sub) Alg. 2 step 1: sample, sort on chip, heavy keys, the
+//                      bucket numbering (light table L, heavy hash table H)
+//   hist     (all)     per-bucket totals of every subproblem
+//   scan     (CTA/sub) bucket starts; children for the next level, on-chip
+//                      base-case tasks, dovetail-merge zones (Alg. 2 step 3)
+//   scatter  (all)     Alg. 2 step 2: stable counting sort by bucket id;
+//                      per-tile warp ranking + decoupled look-back scan
+//   finish   (all)     base case on chip (stable LSD in shared memory) and
+//                      plain copies
+// After the last level, the dovetail merges (Alg. 3 semantics) run from the
+// deepest level up.  Every spin-wait is bounded by %globaltimer and latches
+// DTSORT_ERR_DEVICE_TIMEOUT instead of hanging.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace dts {
+
+constexpr int NT = 512;                       // threads per CTA, every phase
+constexpr int NWARP = NT / 32;
+constexpr int GAMMA_HW = 9;                   // widest digit of one level
+constexpr int NB_HW = (1 << GAMMA_HW) + (1 << (GAMMA_HW - 1)) + 1;  // 769
+constexpr int NB_PAD = 776;                   // NB_HW + dummy bucket, padded
+constexpr int SMAX = 8192;                    // largest on-chip sample
+constexpr int HASH_HW = 1 << GAMMA_HW;        // hash slots for <= 256 heavy keys
+constexpr int MAXLEV = 136;                   // > 2 * 64 + slack
+constexpr int64_t COPY_CHUNK = 1 << 16;       // records per plain-copy task
+constexpr int MERGE_CHUNK = 8192;             // output records per merge item
+constexpr int FIN_DIG = 8;                    // base-case digit bits
+constexpr int FIN_NB = (1 << FIN_DIG) + 8;    // 256 digits + dummy, padded
+constexpr uint16_t HEMPTY = 0xFFFF;
+
+enum { ERR_INVALID = 1, ERR_TIMEOUT = 4, ERR_INTERNAL = 6 };
+enum { TASK_SORT = 0, TASK_COPY = 1 };
+enum { PH_SETUP = 0, PH_SAMPLE, PH_HIST, PH_SCAN, PH_SCATTER, PH_FINISH, PH_MERGE,
+       PH_TOTAL };
+
+// A subproblem: keys in [start, start+size) agree on every bit >= hi.
+struct Seg {
+  int64_t start, size;
+  int64_t ntotal;   // length of the array it came from (n of Alg. 2)
+  int32_t hi;       // low bits still unsorted
+  uint8_t res;      // buffer (0 = caller's, 1 = workspace) the result goes to
+  uint8_t pad[3];
+};
+
+// Per subproblem of the current level, filled by setup + sample.
+struct SegInfo {
+  int32_t gamma;    // planned digit width
+  int32_t lo, t;    // MSD zone digit = key bits [lo, t)
+  int32_t nheavy;
+  int32_t nb;       // 2^(t-lo) + nheavy + 1 (overflow last)
+  int32_t hbits;    // log2 hash capacity (0: no heavy keys)
+  int64_t ntiles, tile0;
+  int64_t boff;     // bucket arrays (counts / starts)
+  int64_t hoff;     // heavy keys, sorted
+  int64_t zoff;     // light table L: 2^(t-lo)+1 entries
+  int64_t hashoff;  // heavy hash table H
+  int64_t soff;     // look-back status words: ntiles x nb
+  int64_t mhoff;    // persistent heavy store reservation (for merges)
+};
+
+struct Task {
+  int64_t start, size;
+  int32_t hi;
+  uint8_t src, dst, kind, pad;
+};
+
+// An MSD zone with heavy buckets, merged after its light bucket is sorted.
+struct MZone {
+  int64_t zs, b0, ze;   // zone [zs, ze); light bucket [zs, zs+b0)
+  int64_t mh;           // its heavy keys / sizes / final starts in the store
+  int64_t chunk0;       // first merge work item
+  int32_t m;            // heavy buckets
+  uint8_t obuf;         // output buffer; inputs are in the other one
+  uint8_t pad[3];
+};
+
+struct Ctl {
+  unsigned bar_count, bar_gen;
+  int error, nlevels;
+  int err_snap;   // error as of the last grid barrier: every CTA decides alike
+  int pad_;
+  long long nseg[2];
+  long long tile_ctr, ntiles;
+  long long ntasks, task_ctr;
+  unsigned long long zone_alloc;  // (zones << 40) | chunks
+  long long mh_alloc;
+  long long merge_ctr;
+  long long lvl_zone[MAXLEV + 1];
+  unsigned long long lvl_chunk[MAXLEV + 1];
+  long long st_segments[16], st_records[16], st_heavy_keys[16],
+      st_heavy_records[16], st_overflow[16];
+  long long st_fin_tasks, st_fin_records, st_copy_records, st_merge_zones,
+      st_merge_records;
+  unsigned long long t_phase[8];
+  unsigned long long t_last;
+};
+
+// Statistics as the host reads them (mirrors the public struct's prefix).
+struct DevStats {
+  int32_t levels, status;
+  int64_t segments[16], records[16], heavy_keys[16], heavy_records[16],
+      overflow_records[16];
+  int64_t finisher_tasks, finisher_records, copy_records, merge_zones,
+      merge_records, learned_fixup_records, learned_fixup_steps;
+  double learned_cv, learned_mom;
+  double phase_ms[8];
+  int64_t reserved[8];
+};
+
+struct Params {
+  void *keys[2];          // [0] caller's arrays, [1] workspace ping-pong copy
+  void *vals[2];          // NULL for key-only
+  int64_t n;
+  const int64_t *offsets; // segmented input (NULL: one array [0, n))
+  int64_t nsegs_in;
+  int32_t key_bits;
+  int32_t gamma_max;
+  int32_t cap;            // largest base-case bucket
+  int32_t heavy_on;
+  int64_t target;         // desired bucket size after distribution
+  uint64_t seed;
+  int32_t sample_factor;  // samples = 2^gamma * L * factor (capped)
+  int32_t debug_fault;    // 1: tile 1 of level 0 never publishes (tests)
+  unsigned long long wait_ns;  // bound of every spin-wait
+  Ctl *ctl;
+  Seg *segs[2];
+  SegInfo *info;
+  int64_t *bcount, *bstart;
+  int32_t *lid;
+  void *heavy;
+  void *hash_keys;
+  uint16_t *hash_ids;
+  unsigned long long *status;
+  Task *tasks;
+  MZone *zones;
+  void *mh_keys;
+  int64_t *mh_sizes, *mh_start;
+  int64_t maxseg, bmax, hmax, zmax, hashmax, swords, tmax, mhmax;
+  int *dev_status;
+  DevStats *stats;
+};
+
+// ------------------------------------------------------------------ helpers
+__device__ __forceinline__ unsigned long long gtimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ unsigned long long ld_relaxed(const unsigned long long *p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_relaxed(unsigned long long *p, unsigned long long v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ long long ld_cg64(const long long *p) {
+  return (long long)__ldcg((const unsigned long long *)p);
+}
+
+// Loads a table entry written in an earlier phase by another SM: through L2
+// only, so that no stale L1 line is ever used.
+template <typename T>
+__device__ __forceinline__ T ldcg_obj(const T *p) {
+  static_assert(sizeof(T) % 8 == 0, "8-byte granular");
+  T r;
+  const unsigned long long *s = (const unsigned long long *)p;
+  unsigned long long *d = (unsigned long long *)&r;
+#pragma unroll
+  for (int i = 0; i < (int)(sizeof(T) / 8); ++i) d[i] = __ldcg(s + i);
+  return r;
+}
+
+__device__ __forceinline__ long long atomic_add_ll(long long *p, long long v) {
+  return (long long)atomicAdd((unsigned long long *)p, (unsigned long long)v);
+}
+
+__device__ __forceinline__ void latch(const Params &P, int code) {
+  atomicCAS(&P.ctl->error, 0, code);
+  atomicCAS(P.dev_status, 0, code);
+}
+
+__device__ __forceinline__ uint64_t sm64_fmix(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+// Output i of the SplitMix64 sequence started from state s.
+__device__ __forceinline__ uint64_t sm64_at(uint64_t s, uint64_t i) {
+  return sm64_fmix(s + (i + 1) * 0x9E3779B97F4A7C15ull);
+}
+
+__device__ __forceinline__ uint64_t lowmask(int bits) {
+  return bits >= 64 ? ~0ull : ((1ull << bits) - 1ull);
+}
+
+__device__ __forceinline__ int bitlen64(uint64_t x) { return x ? 64 - __clzll((long long)x) : 0; }
+
+template <typename K>
+__device__ __forceinline__ K ld_key(const K *p) {
+  if constexpr (sizeof(K) == 4) return (K)__ldcg((const unsigned int *)p);
+  else return (K)__ldcg((const unsigned long long *)p);
+}
+
+template <typename K>
+__device__ __forceinline__ uint32_t hash_slot(K key, int bits) {
+  return (uint32_t)(((uint64_t)key * 0x9E3779B97F4A7C15ull) >> (64 - bits));
+}
+
+// Grid-wide barrier for a cooperatively launched grid (all CTAs resident).
+static __device__ __noinline__ void grid_sync(const Params &P) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    Ctl *c = P.ctl;
+    volatile unsigned *gen = &c->bar_gen;
+    unsigned g = *gen;
+    __threadfence();
+    unsigned arrived = atomicAdd(&c->bar_count, 1u);
+    if (arrived == gridDim.x - 1) {
+      c->bar_count = 0;
+      c->err_snap = *(volatile int *)&c->error;
+      __threadfence();
+      atomicAdd(&c->bar_gen, 1u);
+    } else {
+      unsigned long long t0 = gtimer();
+      while (*gen == g) {
+        __nanosleep(100);
+        if (gtimer() - t0 > P.wait_ns + 3000000000ull) {
+          latch(P, ERR_TIMEOUT);
+          break;
+        }
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+}
+
+// Exclusive scan of one value per thread over the CTA; sh needs NWARP+1.
+template <typename T>
+__device__ __forceinline__ T block_excl_scan(T v, T *sh, T &total) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  T x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    T y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) sh[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    T s = lane < NWARP ? sh[lane] : T(0);
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      T y = __shfl_up_sync(0xffffffffu, s, o);
+      if (lane >= o) s += y;
+    }
+    if (lane < NWARP) sh[lane] = s;
+  }
+  __syncthreads();
+  T base = w ? sh[w - 1] : T(0);
+  total = sh[NWARP - 1];
+  __syncthreads();
+  return base + x - v;
+}
+
+// Rank of this lane's item among the warp's items with the same bucket that
+// come earlier in (round, lane) order; wc is the warp's counter row.
+__device__ __forceinline__ unsigned warp_rank(unsigned b, uint16_t *wc) {
+  const unsigned lane = threadIdx.x & 31;
+  unsigned peers = __match_any_sync(0xffffffffu, b);
+  unsigned leader = __ffs(peers) - 1;
+  unsigned before = __popc(peers & ((1u << lane) - 1u));
+  unsigned old = 0;
+  if (lane == leader) {
+    old = wc[b];
+    wc[b] = (uint16_t)(old + __popc(peers));
+  }
+  old = __shfl_sync(0xffffffffu, old, leader);
+  __syncwarp();
+  return old + before;
+}
+
+// Digit width for a subproblem of size s: the fewest levels (of at most
+// gmax bits each) that bring buckets down to about `target` records, bits
+// spread evenly over those levels.
+__device__ __forceinline__ int plan_gamma(int64_t s, int64_t target, int gmax) {
+  int e = 0;
+  while (e < 62 && (target << e) < s) ++e;
+  if (e < 1) e = 1;
+  int nlev = (e + gmax - 1) / gmax;
+  int g = (e + nlev - 1) / nlev;
+  return g < 1 ? 1 : (g > gmax ? gmax : g);
+}
+
+// ----------------------------------------------------- per-segment tables
+template <typename K>
+struct SegTables {
+  SegInfo info;
+  int64_t start, size;
+  int32_t hi, seg;
+  uint8_t res;
+  int32_t *lid;        // smem, 2^geff + 1
+  K *hkeys;            // smem hash keys
+  uint16_t *hids;      // smem hash ids
+};
+
+// GetBucketId (Alg. 2): heavy keys through H, overflow past the sampled key
+// range, light keys through L by their MSD zone.  Returns nb for nothing.
+template <typename K>
+__device__ __forceinline__ unsigned bucket_of(const SegTables<K> &T, K key) {
+  const SegInfo &I = T.info;
+  if (I.hbits) {
+    const uint32_t cap1 = (1u << I.hbits) - 1u;
+    uint32_t s = hash_slot<K>(key, I.hbits);
+    while (true) {
+      uint16_t id = T.hids[s];
+      if (id == HEMPTY) break;
+      if (T.hkeys[s] == key) return id;
+      s = (s + 1) & cap1;
+    }
+  }
+  uint64_t m = (uint64_t)key & lowmask(T.hi);
+  if (I.t < 64 && (m >> I.t) != 0) return (unsigned)(I.nb - 1);
+  return (unsigned)T.lid[m >> I.lo];
+}
+
+template <typename K>
+__device__ void load_tables(const Params &P, int seg, int level, SegTables<K> &T,
+                            int32_t *lid_s, K *hk_s, uint16_t *hid_s) {
+  // all threads call; T lives in smem
+  if (threadIdx.x == 0) {
+    const Seg S = ldcg_obj(&P.segs[level & 1][seg]);
+    T.info = ldcg_obj(&P.info[seg]);
+    T.start = S.start;
+    T.size = S.size;
+    T.hi = S.hi;
+    T.res = S.res;
+    T.seg = seg;
+    T.lid = lid_s;
+    T.hkeys = hk_s;
+    T.hids = hid_s;
+  }
+  __syncthreads();
+  const int nz = (1 << (T.info.t - T.info.lo)) + 1;
+  for (int i = threadIdx.x; i < nz; i += NT) lid_s[i] = __ldcg(P.lid + T.info.zoff + i);
+  if (T.info.hbits) {
+    const int cap = 1 << T.info.hbits;
+    const K *hk = (const K *)P.hash_keys + T.info.hashoff;
+    for (int i = threadIdx.x; i < cap; i += NT) {
+      hk_s[i] = ld_key<K>(hk + i);
+      hid_s[i] = __ldcg(P.hash_ids + T.info.hashoff + i);
+    }
+  }
+  __syncthreads();
+}
+
+// index of the segment owning global tile t (tile0 increasing)
+__device__ __forceinline__ int find_tile_seg(const Params &P, int64_t nseg, int64_t t) {
+  int64_t lo = 0, hi = nseg - 1;
+  while (lo < hi) {
+    int64_t mid = (lo + hi + 1) >> 1;
+    if (__ldcg((const long long *)&P.info[mid].tile0) <= t) lo = mid;
+    else hi = mid - 1;
+  }
+  return (int)lo;
+}
+
+}  // namespace dts

@@ -1,0 +1,1036 @@
+// Phases of the persistent dtsort kernel (see dtsort_device.cuh).
+#pragma once
+
+#include "dtsort_device.cuh"
+
+namespace dts {
+
+// Compile-time shape of one (key, value) instantiation.
+template <typename K, bool HV>
+struct Shape {
+  static constexpr int KB = sizeof(K);
+  static constexpr int VB = HV ? (int)sizeof(K) : 0;
+  static constexpr int ITEMS = KB == 4 ? 16 : 8;        // scatter items / thread
+  static constexpr int TILE = NT * ITEMS;
+  static constexpr int FIN_BYTES = 96 * 1024;           // base-case data buffers
+  static constexpr int FIN_CAP = FIN_BYTES / (2 * (KB + VB));
+  static constexpr int FIN_IT = FIN_CAP / NT;           // base-case items / thread
+  static constexpr int STAGE = TILE * KB;               // scatter staging (keys or values)
+};
+
+struct Carve {
+  unsigned char *p;
+  __device__ explicit Carve(unsigned char *q) : p(q) {}
+  template <typename T>
+  __device__ T *take(size_t n) {
+    uintptr_t a = ((uintptr_t)p + 15) & ~(uintptr_t)15;
+    p = (unsigned char *)(a + n * sizeof(T));
+    return (T *)a;
+  }
+};
+
+template <typename K, bool HV>
+constexpr size_t smem_bytes() {
+  using S = Shape<K, HV>;
+  // scatter
+  size_t sc = 0;
+  sc += 64 + sizeof(SegTables<K>);
+  sc += 16 + 4 * ((1 << GAMMA_HW) + 1);            // lid
+  sc += 16 + sizeof(K) * HASH_HW + 16 + 2 * HASH_HW;  // hash
+  sc += 16 + (size_t)S::STAGE;                     // key / value staging
+  sc += 16 + 2 * (size_t)S::TILE;                  // bucket of each staged slot
+  sc += 16 + 2 * (size_t)NWARP * NB_PAD;           // warp counters
+  sc += 16 + 4 * NB_PAD * 2 + 16 + 8 * NB_PAD;     // tile counts/offsets, bases
+  sc += 16 + 8 * (NWARP + 1) + 256;
+  // base case
+  size_t fin = 0;
+  fin += 16 + (size_t)S::FIN_BYTES;
+  fin += 16 + 2 * (size_t)NWARP * FIN_NB;
+  fin += 16 + 4 * FIN_NB * 2;
+  fin += 16 + 8 * (NWARP + 1) + 256;
+  // sampler
+  size_t smp = 16 + sizeof(K) * SMAX + 16 + sizeof(K) * (SMAX / 2 + 8) + 16 + 4 * 1024 +
+               16 + sizeof(K) * HASH_HW + 16 + 2 * HASH_HW + 512;
+  size_t m = sc > fin ? sc : fin;
+  return m > smp ? m : smp;
+}
+
+// ----------------------------------------------------------------- queues
+__device__ __forceinline__ void push_task(const Params &P, const Task &t) {
+  long long i = atomic_add_ll(&P.ctl->ntasks, 1ll);
+  if (i >= P.tmax) {
+    latch(P, ERR_INTERNAL);
+    return;
+  }
+  P.tasks[i] = t;
+}
+
+__device__ __forceinline__ void push_copy(const Params &P, int64_t start, int64_t size,
+                                          int src, int dst) {
+  if (size <= 0 || src == dst) return;
+  for (int64_t a = 0; a < size; a += COPY_CHUNK) {
+    Task t;
+    t.start = start + a;
+    t.size = size - a < COPY_CHUNK ? size - a : COPY_CHUNK;
+    t.hi = 0;
+    t.src = (uint8_t)src;
+    t.dst = (uint8_t)dst;
+    t.kind = TASK_COPY;
+    push_task(P, t);
+  }
+}
+
+__device__ __forceinline__ void push_seg(const Params &P, int list, const Seg &s) {
+  long long i = atomic_add_ll(&P.ctl->nseg[list], 1ll);
+  if (i >= P.maxseg) {
+    latch(P, ERR_INTERNAL);
+    return;
+  }
+  P.segs[list][i] = s;
+}
+
+// A bucket that still needs work: recurse, sort on chip, or just move it.
+__device__ __forceinline__ void emit_child(const Params &P, int next_list, int64_t start,
+                                           int64_t size, int hi, int data_buf, int res_buf,
+                                           int64_t ntotal) {
+  if (size <= 0) return;
+  if (hi == 0 || size == 1) {
+    push_copy(P, start, size, data_buf, res_buf);
+  } else if (size <= P.cap) {
+    Task t;
+    t.start = start;
+    t.size = size;
+    t.hi = hi;
+    t.src = (uint8_t)data_buf;
+    t.dst = (uint8_t)res_buf;
+    t.kind = TASK_SORT;
+    push_task(P, t);
+  } else {
+    Seg s;
+    s.start = start;
+    s.size = size;
+    s.ntotal = ntotal;
+    s.hi = hi;
+    s.res = (uint8_t)res_buf;
+    push_seg(P, next_list, s);
+  }
+}
+
+// ------------------------------------------------------------------- seed
+template <typename K, bool HV>
+__device__ void phase_seed(const Params &P) {
+  const int64_t S = P.offsets ? P.nsegs_in : 1;
+  for (int64_t i = (int64_t)blockIdx.x * NT + threadIdx.x; i < S;
+       i += (int64_t)gridDim.x * NT) {
+    int64_t a = 0, b = P.n;
+    if (P.offsets) {
+      a = (int64_t)__ldcg((const unsigned long long *)P.offsets + i);
+      b = (int64_t)__ldcg((const unsigned long long *)P.offsets + i + 1);
+      bool bad = b < a || a < 0 || b > P.n || (i == 0 && a != 0) || (i == S - 1 && b != P.n);
+      if (bad) {
+        latch(P, ERR_INVALID);
+        continue;
+      }
+    }
+    emit_child(P, 0, a, b - a, P.key_bits, 0, 0, b - a);
+  }
+}
+
+// ------------------------------------------------------------------ setup
+template <typename K, bool HV>
+__device__ void phase_setup(const Params &P, int level, unsigned char *smem) {
+  using S = Shape<K, HV>;
+  Ctl *c = P.ctl;
+  const int p = level & 1;
+  const int64_t nseg = min(ld_cg64(&c->nseg[p]), (long long)P.maxseg);
+  long long *sh = (long long *)smem;  // NWARP+1 scratch
+  int64_t cr_tiles = 0, cr_b = 0, cr_h = 0, cr_z = 0, cr_hash = 0, cr_st = 0, cr_rec = 0;
+  for (int64_t base = 0; base < nseg; base += NT) {
+    const int64_t i = base + threadIdx.x;
+    int64_t tiles = 0, nbm = 0, hm = 0, zm = 0, hsm = 0, stm = 0, sz = 0;
+    int g = 0;
+    if (i < nseg) {
+      const Seg s = ldcg_obj(&P.segs[p][i]);
+      sz = s.size;
+      g = plan_gamma(s.size, P.target, P.gamma_max);
+      tiles = (s.size + S::TILE - 1) / S::TILE;
+      nbm = (1 << g) + (1 << (g - 1)) + 1;
+      hm = 1 << (g - 1);
+      zm = (1 << g) + 1;
+      hsm = 1 << g;
+      stm = tiles * nbm;
+    }
+    long long tot;
+    const int64_t o_t = block_excl_scan<long long>(tiles, sh, tot) + cr_tiles; cr_tiles += tot;
+    const int64_t o_b = block_excl_scan<long long>(nbm, sh, tot) + cr_b; cr_b += tot;
+    const int64_t o_h = block_excl_scan<long long>(hm, sh, tot) + cr_h; cr_h += tot;
+    const int64_t o_z = block_excl_scan<long long>(zm, sh, tot) + cr_z; cr_z += tot;
+    const int64_t o_hs = block_excl_scan<long long>(hsm, sh, tot) + cr_hash; cr_hash += tot;
+    const int64_t o_s = block_excl_scan<long long>(stm, sh, tot) + cr_st; cr_st += tot;
+    block_excl_scan<long long>(sz, sh, tot); cr_rec += tot;
+    if (i < nseg) {
+      SegInfo I;
+      I.gamma = g;
+      I.lo = I.t = 0;
+      I.nheavy = 0;
+      I.nb = 0;
+      I.hbits = 0;
+      I.ntiles = tiles;
+      I.tile0 = o_t;
+      I.boff = o_b;
+      I.hoff = o_h;
+      I.zoff = o_z;
+      I.hashoff = o_hs;
+      I.soff = o_s;
+      I.mhoff = 0;
+      P.info[i] = I;
+    }
+  }
+  if (threadIdx.x == 0) {
+    if (cr_b > P.bmax || cr_h > P.hmax || cr_z > P.zmax || cr_hash > P.hashmax ||
+        cr_st > P.swords) {
+      latch(P, ERR_INTERNAL);
+    }
+    c->ntiles = cr_tiles;
+    c->tile_ctr = 0;
+    c->task_ctr = 0;
+    c->merge_ctr = 0;
+    c->nseg[p ^ 1] = 0;
+    if (level > 0) c->ntasks = 0;
+    const unsigned long long za = __ldcg(&c->zone_alloc);
+    c->lvl_zone[level] = (long long)(za >> 40);
+    c->lvl_chunk[level] = za & ((1ull << 40) - 1);
+    const int l = level < 15 ? level : 15;
+    c->st_segments[l] += nseg;
+    c->st_records[l] += cr_rec;
+  }
+}
+
+// ----------------------------------------------------------------- sample
+template <typename K, bool HV>
+__device__ void phase_sample(const Params &P, int level, unsigned char *smem) {
+  Ctl *c = P.ctl;
+  const int p = level & 1;
+  const int64_t nseg = min(ld_cg64(&c->nseg[p]), (long long)P.maxseg);
+  const K *src = (const K *)P.keys[level & 1];
+  Carve cv(smem);
+  K *Ssm = cv.take<K>(SMAX);
+  K *hv = cv.take<K>(SMAX / 2 + 8);
+  K *hk = cv.take<K>(HASH_HW);
+  uint16_t *hid = cv.take<uint16_t>(HASH_HW);
+  long long *sh = cv.take<long long>(NWARP + 1);
+  long long *resv = cv.take<long long>(1);
+  for (int64_t si = blockIdx.x; si < nseg; si += gridDim.x) {
+    const Seg S = ldcg_obj(&P.segs[p][si]);
+    SegInfo I = ldcg_obj(&P.info[si]);
+    const int g = I.gamma;
+    const int64_t nbm = (1 << g) + (1 << (g - 1)) + 1;
+    for (int64_t b = threadIdx.x; b < nbm; b += NT) P.bcount[I.boff + b] = 0;
+    int L = 0;
+    while (L < 63 && (1ll << L) < S.ntotal) ++L;
+    if (L < 1) L = 1;
+    int64_t m = ((int64_t)1 << g) * L * (int64_t)P.sample_factor;
+    if (m > SMAX) m = SMAX;
+    int M = 1;
+    while (M < m) M <<= 1;
+    const uint64_t st = P.seed ^ (uint64_t)S.start ^ ((uint64_t)S.size * 0x9E3779B97F4A7C15ull) ^
+                        ((uint64_t)S.hi << 57);
+    for (int k = threadIdx.x; k < M; k += NT) {
+      if (k < m) {
+        const int64_t pos = S.start + (int64_t)(sm64_at(st, (uint64_t)k) % (uint64_t)S.size);
+        Ssm[k] = ld_key<K>(src + pos);
+      } else {
+        Ssm[k] = (K)~(K)0;
+      }
+    }
+    __syncthreads();
+    // bitonic sort of the sample on chip
+    for (int kk = 2; kk <= M; kk <<= 1) {
+      for (int j = kk >> 1; j > 0; j >>= 1) {
+        for (int i = threadIdx.x; i < M; i += NT) {
+          const int ixj = i ^ j;
+          if (ixj > i) {
+            const K a = Ssm[i], b = Ssm[ixj];
+            const bool up = (i & kk) == 0;
+            if ((a > b) == up) {
+              Ssm[i] = b;
+              Ssm[ixj] = a;
+            }
+          }
+        }
+        __syncthreads();
+      }
+    }
+    // key range from the largest sample (overflow bucket above it)
+    const uint64_t rmax = (uint64_t)Ssm[m - 1] & lowmask(S.hi);
+    const int t = bitlen64(rmax);
+    const int lo = t - g > 0 ? t - g : 0;
+    const int geff = t - lo;
+    // heavy keys: seen at least twice among S[L-1], S[2L-1], ...
+    int nh = 0;
+    if (P.heavy_on) {
+      const int64_t nsub = m / L;
+      long long carry = 0;
+      for (int64_t base = 0; base < nsub; base += NT) {
+        const int64_t j = base + threadIdx.x;
+        int first = 0;
+        K a = 0;
+        if (j + 1 < nsub) {
+          a = Ssm[(j + 1) * L - 1];
+          const K b = Ssm[(j + 2) * L - 1];
+          first = (a == b) && (j == 0 || Ssm[j * L - 1] != a);
+        }
+        long long tot;
+        const long long o = block_excl_scan<long long>(first, sh, tot) + carry;
+        if (first && o < (SMAX / 2 + 8)) hv[o] = a;
+        carry += tot;
+      }
+      nh = (int)carry;
+      const int hcap = 1 << (g - 1);
+      if (nh > hcap) nh = hcap;
+      if (nh > 0) {
+        // room for this subproblem's heavy buckets in the merge store
+        if (threadIdx.x == 0) {
+          const long long off = atomic_add_ll(&c->mh_alloc, (long long)nh);
+          *resv = (off + nh > P.mhmax) ? -1 : off;
+        }
+        __syncthreads();
+        const long long off = *resv;
+        __syncthreads();
+        if (off < 0) nh = 0;  // store full: plain digit buckets for this one
+        else I.mhoff = off;
+      }
+    }
+    // heavy list out; light table L[z] = z + #heavy keys in zones < z
+    for (int j = threadIdx.x; j < nh; j += NT) ((K *)P.heavy)[I.hoff + j] = hv[j];
+    const int nz = 1 << geff;
+    for (int z = threadIdx.x; z <= nz; z += NT) {
+      int a = 0, b = nh;
+      while (a < b) {
+        const int mid = (a + b) >> 1;
+        const uint64_t zm = ((uint64_t)hv[mid] & lowmask(S.hi)) >> lo;
+        if (zm < (uint64_t)z) a = mid + 1;
+        else b = mid;
+      }
+      P.lid[I.zoff + z] = z + a;
+    }
+    int hbits = 0;
+    if (nh > 0) {
+      hbits = 1;
+      while ((1 << hbits) < 2 * nh) ++hbits;
+      const int cap = 1 << hbits;
+      for (int i = threadIdx.x; i < cap; i += NT) hid[i] = HEMPTY;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        for (int j = 0; j < nh; ++j) {
+          const K key = hv[j];
+          const int zone = (int)(((uint64_t)key & lowmask(S.hi)) >> lo);
+          uint32_t s = hash_slot<K>(key, hbits);
+          while (hid[s] != HEMPTY) s = (s + 1) & (uint32_t)(cap - 1);
+          hk[s] = key;
+          hid[s] = (uint16_t)(zone + j + 1);
+        }
+      }
+      __syncthreads();
+      K *HK = (K *)P.hash_keys + I.hashoff;
+      for (int i = threadIdx.x; i < cap; i += NT) {
+        HK[i] = hk[i];
+        P.hash_ids[I.hashoff + i] = hid[i];
+      }
+    }
+    if (threadIdx.x == 0) {
+      I.lo = lo;
+      I.t = t;
+      I.nheavy = nh;
+      I.nb = nz + nh + 1;
+      I.hbits = hbits;
+      P.info[si] = I;
+      atomic_add_ll(&c->st_heavy_keys[level < 15 ? level : 15], (long long)nh);
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------- histogram
+template <typename K, bool HV>
+__device__ void phase_hist(const Params &P, int level, unsigned char *smem) {
+  using S = Shape<K, HV>;
+  Ctl *c = P.ctl;
+  const int64_t nseg = min(ld_cg64(&c->nseg[level & 1]), (long long)P.maxseg);
+  const int64_t ntiles = ld_cg64(&c->ntiles);
+  if (ntiles == 0) return;
+  const K *src = (const K *)P.keys[level & 1];
+  Carve cv(smem);
+  SegTables<K> &T = *cv.take<SegTables<K>>(1);
+  int32_t *lid_s = cv.take<int32_t>((1 << GAMMA_HW) + 1);
+  K *hk_s = cv.take<K>(HASH_HW);
+  uint16_t *hid_s = cv.take<uint16_t>(HASH_HW);
+  unsigned *cnt = cv.take<unsigned>(NB_PAD);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t t0 = ntiles * blockIdx.x / gridDim.x;
+  const int64_t t1 = ntiles * (blockIdx.x + 1) / gridDim.x;
+  int cur = -1;
+  auto flush = [&]() {
+    __syncthreads();
+    for (int b = threadIdx.x; b < T.info.nb; b += NT)
+      if (cnt[b]) atomicAdd((unsigned long long *)&P.bcount[T.info.boff + b],
+                            (unsigned long long)cnt[b]);
+    __syncthreads();
+  };
+  for (int64_t t = t0; t < t1; ++t) {
+    int s = cur;
+    if (cur < 0 || t >= T.info.tile0 + T.info.ntiles) s = find_tile_seg(P, nseg, t);
+    if (s != cur) {
+      if (cur >= 0) flush();
+      load_tables<K>(P, s, level, T, lid_s, hk_s, hid_s);
+      for (int b = threadIdx.x; b < NB_PAD; b += NT) cnt[b] = 0;
+      __syncthreads();
+      cur = s;
+    }
+    const int nb = T.info.nb;
+    const int64_t row = T.info.soff + (t - T.info.tile0) * nb;
+    for (int b = threadIdx.x; b < nb; b += NT) P.status[row + b] = 0ull;
+    const int64_t base = T.start + (t - T.info.tile0) * S::TILE;
+    const int64_t rem = T.start + T.size - base;
+    const int tn = rem < S::TILE ? (int)rem : S::TILE;
+#pragma unroll 4
+    for (int j = 0; j < S::ITEMS; ++j) {
+      const int i = w * 32 * S::ITEMS + j * 32 + lane;
+      unsigned b = (unsigned)nb;
+      if (i < tn) b = bucket_of<K>(T, ld_key<K>(src + base + i));
+      const unsigned peers = __match_any_sync(0xffffffffu, b);
+      if (lane == __ffs(peers) - 1) atomicAdd(&cnt[b], (unsigned)__popc(peers));
+    }
+  }
+  if (cur >= 0) flush();
+}
+
+// ------------------------------------------------------------------- scan
+template <typename K, bool HV>
+__device__ void phase_scan(const Params &P, int level, unsigned char *smem) {
+  Ctl *c = P.ctl;
+  const int p = level & 1;
+  const int64_t nseg = min(ld_cg64(&c->nseg[p]), (long long)P.maxseg);
+  const int srcb = level & 1, dstb = srcb ^ 1;
+  Carve cv(smem);
+  long long *cntv = cv.take<long long>(NB_PAD);
+  long long *excl = cv.take<long long>(NB_PAD + 1);
+  int32_t *lid_s = cv.take<int32_t>((1 << GAMMA_HW) + 1);
+  long long *sh = cv.take<long long>(NWARP + 1);
+  for (int64_t si = blockIdx.x; si < nseg; si += gridDim.x) {
+    const Seg S = ldcg_obj(&P.segs[p][si]);
+    const SegInfo I = ldcg_obj(&P.info[si]);
+    const int nb = I.nb;
+    // bucket starts: two buckets per thread, one CTA-wide scan
+    for (int b = threadIdx.x; b < NB_PAD; b += NT)
+      cntv[b] = b < nb ? (long long)__ldcg((const unsigned long long *)&P.bcount[I.boff + b]) : 0;
+    __syncthreads();
+    const int i0 = 2 * threadIdx.x, i1 = i0 + 1;
+    const long long v0 = i0 < NB_PAD ? cntv[i0] : 0;
+    const long long v1 = i1 < NB_PAD ? cntv[i1] : 0;
+    long long tot;
+    const long long o = block_excl_scan<long long>(v0 + v1, sh, tot);
+    if (i0 < NB_PAD) excl[i0] = o;
+    if (i1 < NB_PAD) excl[i1] = o + v0;
+    if (threadIdx.x == 0) excl[NB_PAD] = tot;
+    const int nz = 1 << (I.t - I.lo);
+    for (int z = threadIdx.x; z <= nz; z += NT) lid_s[z] = __ldcg(P.lid + I.zoff + z);
+    __syncthreads();
+    for (int b = threadIdx.x; b < nb; b += NT) P.bstart[I.boff + b] = S.start + excl[b];
+    const int res = S.res;
+    long long heavy_recs = 0;
+    for (int z = threadIdx.x; z < nz; z += NT) {
+      const int lb = lid_s[z], le = lid_s[z + 1];
+      const int m = le - lb - 1;
+      const int64_t zs = S.start + excl[lb];
+      const int64_t b0 = cntv[lb];
+      const int64_t ze = S.start + excl[le];
+      int light_res = res;
+      if (m > 0) {
+        light_res = res ^ 1;  // the merge reads from the other buffer
+        const int64_t nch = (ze - zs + MERGE_CHUNK - 1) / MERGE_CHUNK;
+        const unsigned long long old =
+            atomicAdd(&c->zone_alloc, (1ull << 40) | (unsigned long long)nch);
+        const int64_t zidx = (int64_t)(old >> 40);
+        const int64_t mh = I.mhoff + (lb - z);
+        for (int q = 0; q < m; ++q) {
+          ((K *)P.mh_keys)[mh + q] = ld_key<K>((const K *)P.heavy + I.hoff + (lb - z) + q);
+          P.mh_sizes[mh + q] = cntv[lb + 1 + q];
+        }
+        MZone Z;
+        Z.zs = zs;
+        Z.b0 = b0;
+        Z.ze = ze;
+        Z.mh = mh;
+        Z.chunk0 = (int64_t)(old & ((1ull << 40) - 1));
+        Z.m = m;
+        Z.obuf = (uint8_t)res;
+        if (zidx < P.mhmax) P.zones[zidx] = Z;
+        else latch(P, ERR_INTERNAL);
+        heavy_recs += ze - zs - b0;
+        // heavy runs must sit in the merge's input buffer
+        if (dstb == res) push_copy(P, zs + b0, ze - zs - b0, dstb, dstb ^ 1);
+      }
+      emit_child(P, p ^ 1, zs, b0, I.lo, dstb, light_res, S.ntotal);
+    }
+    if (threadIdx.x == 0) {
+      const int ob = nb - 1;
+      const int64_t os = S.start + excl[ob], ol = cntv[ob];
+      if (ol > 0) {
+        emit_child(P, p ^ 1, os, ol, S.hi, dstb, res, S.ntotal);
+        atomic_add_ll(&c->st_overflow[level < 15 ? level : 15], (long long)ol);
+      }
+    }
+    if (heavy_recs) atomic_add_ll(&c->st_heavy_records[level < 15 ? level : 15], heavy_recs);
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------- scatter
+template <typename K, bool HV>
+__device__ void phase_scatter(const Params &P, int level, unsigned char *smem) {
+  using S = Shape<K, HV>;
+  Ctl *c = P.ctl;
+  const int64_t nseg = min(ld_cg64(&c->nseg[level & 1]), (long long)P.maxseg);
+  const int64_t ntiles = ld_cg64(&c->ntiles);
+  const int srcb = level & 1, dstb = srcb ^ 1;
+  const K *src = (const K *)P.keys[srcb];
+  K *dst = (K *)P.keys[dstb];
+  const K *vsrc = HV ? (const K *)P.vals[srcb] : nullptr;
+  K *vdst = HV ? (K *)P.vals[dstb] : nullptr;
+  Carve cv(smem);
+  SegTables<K> &T = *cv.take<SegTables<K>>(1);
+  int32_t *lid_s = cv.take<int32_t>((1 << GAMMA_HW) + 1);
+  K *hk_s = cv.take<K>(HASH_HW);
+  uint16_t *hid_s = cv.take<uint16_t>(HASH_HW);
+  K *stage = cv.take<K>(S::TILE);
+  uint16_t *bid = cv.take<uint16_t>(S::TILE);
+  uint16_t *wcnt = cv.take<uint16_t>(NWARP * NB_PAD);
+  unsigned *tcnt = cv.take<unsigned>(NB_PAD);
+  unsigned *toff = cv.take<unsigned>(NB_PAD);
+  long long *gbase = cv.take<long long>(NB_PAD);
+  unsigned *sh = cv.take<unsigned>(NWARP + 1);
+  long long *tile_sh = cv.take<long long>(1);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  uint16_t *mywc = wcnt + w * NB_PAD;
+  int cur = -1;
+  while (true) {
+    if (threadIdx.x == 0) *tile_sh = atomic_add_ll(&c->tile_ctr, 1ll);
+    __syncthreads();
+    const int64_t t = *tile_sh;
+    if (t >= ntiles) break;
+    int s = cur;
+    if (cur < 0 || t < T.info.tile0 || t >= T.info.tile0 + T.info.ntiles)
+      s = find_tile_seg(P, nseg, t);
+    if (s != cur) {
+      load_tables<K>(P, s, level, T, lid_s, hk_s, hid_s);
+      cur = s;
+    }
+    const int nb = T.info.nb;
+    const int64_t lt = t - T.info.tile0;
+    const int64_t base = T.start + lt * S::TILE;
+    const int64_t rem = T.start + T.size - base;
+    const int tn = rem < S::TILE ? (int)rem : S::TILE;
+    for (int i = threadIdx.x; i < NWARP * NB_PAD; i += NT) wcnt[i] = 0;
+    __syncthreads();
+    // keys in, bucket ids, warp ranks (item order = input order)
+    K key[S::ITEMS];
+    unsigned br[S::ITEMS];  // bucket << 16 | rank within warp
+#pragma unroll
+    for (int j = 0; j < S::ITEMS; ++j) {
+      const int i = w * 32 * S::ITEMS + j * 32 + lane;
+      key[j] = i < tn ? ld_key<K>(src + base + i) : (K)0;
+    }
+#pragma unroll
+    for (int j = 0; j < S::ITEMS; ++j) {
+      const int i = w * 32 * S::ITEMS + j * 32 + lane;
+      unsigned b = (unsigned)nb;
+      if (i < tn) b = bucket_of<K>(T, key[j]);
+      const unsigned r = warp_rank(b, mywc);
+      br[j] = (b << 16) | r;
+    }
+    __syncthreads();
+    // per bucket: exclusive prefix over warps, tile total
+    for (int b = threadIdx.x; b < nb; b += NT) {
+      unsigned run = 0;
+#pragma unroll
+      for (int q = 0; q < NWARP; ++q) {
+        const unsigned x = wcnt[q * NB_PAD + b];
+        wcnt[q * NB_PAD + b] = (uint16_t)run;
+        run += x;
+      }
+      tcnt[b] = run;
+    }
+    __syncthreads();
+    {
+      const int b0 = 2 * threadIdx.x, b1 = b0 + 1;
+      const unsigned v0 = b0 < nb ? tcnt[b0] : 0u, v1 = b1 < nb ? tcnt[b1] : 0u;
+      unsigned tot;
+      const unsigned o = block_excl_scan<unsigned>(v0 + v1, sh, tot);
+      if (b0 < NB_PAD) toff[b0] = o;
+      if (b1 < NB_PAD) toff[b1] = o + v0;
+    }
+    __syncthreads();
+    // decoupled look-back across the segment's tiles, one thread per bucket
+    const int64_t srow = T.info.soff + lt * nb;
+    const bool mute = P.debug_fault == 1 && level == 0 && t == 1;
+    for (int b = threadIdx.x; b < nb; b += NT) {
+      const unsigned long long agg = tcnt[b];
+      long long excl;
+      if (lt == 0) {
+        excl = __ldcg((const long long *)&P.bstart[T.info.boff + b]);
+        st_relaxed(&P.status[srow + b], (2ull << 62) | (unsigned long long)(excl + (long long)agg));
+      } else {
+        if (!mute) st_relaxed(&P.status[srow + b], (1ull << 62) | agg);
+        long long acc = 0;
+        int64_t q = lt - 1;
+        const unsigned long long tstart = gtimer();
+        bool timed_out = false;
+        while (true) {
+          const unsigned long long v = ld_relaxed(&P.status[T.info.soff + q * nb + b]);
+          const unsigned f = (unsigned)(v >> 62);
+          if (f == 0) {
+            if (gtimer() - tstart > P.wait_ns) {
+              timed_out = true;
+              break;
+            }
+            continue;
+          }
+          acc += (long long)(v & ((1ull << 62) - 1));
+          if (f == 2) break;
+          --q;
+        }
+        excl = acc;
+        if (timed_out) {
+          // latch first, then publish, so a successor that reads this status
+          // also sees the error and writes nothing
+          latch(P, ERR_TIMEOUT);
+          __threadfence();
+        }
+        if (!mute)
+          st_relaxed(&P.status[srow + b], (2ull << 62) | (unsigned long long)(excl + (long long)agg));
+      }
+      gbase[b] = excl - (long long)toff[b];
+    }
+    __syncthreads();
+    // after an error nothing more is written; every destination is also
+    // checked against the subproblem's range
+    __threadfence();
+    const bool stop = *(volatile int *)&c->error != 0;
+    const int64_t lo_ok = T.start, hi_ok = T.start + T.size;
+    // stage keys in bucket order, then write each bucket's run contiguously
+    unsigned pos[S::ITEMS];
+#pragma unroll
+    for (int j = 0; j < S::ITEMS; ++j) {
+      const int i = w * 32 * S::ITEMS + j * 32 + lane;
+      pos[j] = 0xFFFFFFFFu;
+      if (i < tn) {
+        const unsigned b = br[j] >> 16;
+        pos[j] = toff[b] + wcnt[w * NB_PAD + b] + (br[j] & 0xFFFFu);
+        stage[pos[j]] = key[j];
+        bid[pos[j]] = (uint16_t)b;
+      }
+    }
+    __syncthreads();
+    if (!stop) {
+      for (int q = threadIdx.x; q < tn; q += NT) {
+        const int64_t d = gbase[bid[q]] + q;
+        if (d >= lo_ok && d < hi_ok) dst[d] = stage[q];
+        else latch(P, ERR_INTERNAL);
+      }
+    }
+    if constexpr (HV) {
+      __syncthreads();
+#pragma unroll
+      for (int j = 0; j < S::ITEMS; ++j) {
+        const int i = w * 32 * S::ITEMS + j * 32 + lane;
+        if (i < tn) stage[pos[j]] = ld_key<K>(vsrc + base + i);
+      }
+      __syncthreads();
+      if (!stop) {
+        for (int q = threadIdx.x; q < tn; q += NT) {
+          const int64_t d = gbase[bid[q]] + q;
+          if (d >= lo_ok && d < hi_ok) vdst[d] = stage[q];
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------- base case + copy
+template <typename K, bool HV>
+__device__ void phase_finish(const Params &P, int level, unsigned char *smem) {
+  using S = Shape<K, HV>;
+  Ctl *c = P.ctl;
+  const int64_t ntasks = min(ld_cg64(&c->ntasks), (long long)P.tmax);
+  Carve cv(smem);
+  K *ka = cv.take<K>(S::FIN_CAP);
+  K *kb = cv.take<K>(S::FIN_CAP);
+  K *va = HV ? cv.take<K>(S::FIN_CAP) : nullptr;
+  K *vb = HV ? cv.take<K>(S::FIN_CAP) : nullptr;
+  uint16_t *wcnt = cv.take<uint16_t>(NWARP * FIN_NB);
+  unsigned *dcnt = cv.take<unsigned>(FIN_NB);
+  unsigned *doff = cv.take<unsigned>(FIN_NB);
+  unsigned *sh = cv.take<unsigned>(NWARP + 1);
+  long long *task_sh = cv.take<long long>(1);
+  int *flag_sh = cv.take<int>(1);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  uint16_t *mywc = wcnt + w * FIN_NB;
+  long long my_recs = 0, my_tasks = 0, my_copy = 0;
+  while (true) {
+    if (threadIdx.x == 0) *task_sh = atomic_add_ll(&c->task_ctr, 1ll);
+    __syncthreads();
+    const int64_t ti = *task_sh;
+    __syncthreads();
+    if (ti >= ntasks) break;
+    const Task tk = ldcg_obj(&P.tasks[ti]);
+    const K *ksrc = (const K *)P.keys[tk.src];
+    K *kdst = (K *)P.keys[tk.dst];
+    const K *vsrc = HV ? (const K *)P.vals[tk.src] : nullptr;
+    K *vdst = HV ? (K *)P.vals[tk.dst] : nullptr;
+    if (tk.kind == TASK_COPY) {
+      for (int64_t i = threadIdx.x; i < tk.size; i += NT) {
+        kdst[tk.start + i] = ld_key<K>(ksrc + tk.start + i);
+        if constexpr (HV) vdst[tk.start + i] = ld_key<K>(vsrc + tk.start + i);
+      }
+      my_copy += tk.size;
+      continue;
+    }
+    const int n = (int)tk.size;
+    for (int i = threadIdx.x; i < n; i += NT) {
+      ka[i] = ld_key<K>(ksrc + tk.start + i);
+      if constexpr (HV) va[i] = ld_key<K>(vsrc + tk.start + i);
+    }
+    __syncthreads();
+    K *kin = ka, *kout = kb, *vin = va, *vout = vb;
+    const int passes = (tk.hi + FIN_DIG - 1) / FIN_DIG;
+    for (int q = 0; q < passes; ++q) {
+      const int shift = q * FIN_DIG;
+      const int bits = tk.hi - shift < FIN_DIG ? tk.hi - shift : FIN_DIG;
+      const unsigned dmask = (1u << bits) - 1u;
+      for (int i = threadIdx.x; i < NWARP * FIN_NB; i += NT) wcnt[i] = 0;
+      __syncthreads();
+      unsigned dr[S::FIN_IT];
+#pragma unroll
+      for (int j = 0; j < S::FIN_IT; ++j) {
+        const int i = w * 32 * S::FIN_IT + j * 32 + lane;
+        dr[j] = 0xFFFFFFFFu;
+        if (w * 32 * S::FIN_IT + j * 32 < n) {  // warp-uniform
+          unsigned d = 1u << FIN_DIG;  // dummy digit
+          if (i < n) d = (unsigned)((uint64_t)kin[i] >> shift) & dmask;
+          const unsigned r = warp_rank(d, mywc);
+          dr[j] = (d << 16) | r;
+        }
+      }
+      __syncthreads();
+      if (threadIdx.x < (1 << FIN_DIG)) {
+        const int d = threadIdx.x;
+        unsigned run = 0;
+#pragma unroll
+        for (int qq = 0; qq < NWARP; ++qq) {
+          const unsigned x = wcnt[qq * FIN_NB + d];
+          wcnt[qq * FIN_NB + d] = (uint16_t)run;
+          run += x;
+        }
+        dcnt[d] = run;
+      }
+      if (threadIdx.x == 0) *flag_sh = 0;
+      __syncthreads();
+      {
+        const unsigned v = threadIdx.x < (1 << FIN_DIG) ? dcnt[threadIdx.x] : 0u;
+        if (v == (unsigned)n) *flag_sh = 1;  // one digit holds everything
+        unsigned tot;
+        const unsigned o = block_excl_scan<unsigned>(v, sh, tot);
+        if (threadIdx.x < (1 << FIN_DIG)) doff[threadIdx.x] = o;
+      }
+      __syncthreads();
+      if (*flag_sh) continue;  // pass would be the identity
+#pragma unroll
+      for (int j = 0; j < S::FIN_IT; ++j) {
+        const int i = w * 32 * S::FIN_IT + j * 32 + lane;
+        if (i < n) {
+          const unsigned d = dr[j] >> 16;
+          const unsigned pp = doff[d] + wcnt[w * FIN_NB + d] + (dr[j] & 0xFFFFu);
+          kout[pp] = kin[i];
+          if constexpr (HV) vout[pp] = vin[i];
+        }
+      }
+      __syncthreads();
+      K *tk_ = kin; kin = kout; kout = tk_;
+      if constexpr (HV) { K *tv = vin; vin = vout; vout = tv; }
+    }
+    for (int i = threadIdx.x; i < n; i += NT) {
+      kdst[tk.start + i] = kin[i];
+      if constexpr (HV) vdst[tk.start + i] = vin[i];
+    }
+    __syncthreads();
+    my_recs += n;
+    my_tasks += 1;
+  }
+  if (threadIdx.x == 0) {
+    if (my_tasks) atomic_add_ll(&c->st_fin_tasks, my_tasks);
+    if (my_recs) atomic_add_ll(&c->st_fin_records, my_recs);
+    if (my_copy) atomic_add_ll(&c->st_copy_records, my_copy);
+  }
+}
+
+// ------------------------------------------------------------------ merge
+// Dovetail merging (Alg. 3): in each zone the sorted light bucket B0 and the
+// heavy buckets B1..Bm are interleaved.  Heavy bucket i starts at
+// zs + lower_bound(B0, k_i) + sum_{i'<i} |B_i'| (the binary searches of
+// Alg. 3); every other position takes the next light record.
+template <typename K, bool HV>
+__device__ void phase_merge_prep(const Params &P, int level, unsigned char *smem) {
+  Ctl *c = P.ctl;
+  const int64_t z0 = min(ld_cg64(&c->lvl_zone[level]), (long long)P.mhmax);
+  const int64_t z1 = min(ld_cg64(&c->lvl_zone[level + 1]), (long long)P.mhmax);
+  long long *sh = (long long *)smem;
+  for (int64_t zi = z0 + blockIdx.x; zi < z1; zi += gridDim.x) {
+    const MZone Z = ldcg_obj(&P.zones[zi]);
+    const K *B0 = (const K *)P.keys[Z.obuf ^ 1] + Z.zs;
+    const int q = threadIdx.x;
+    long long sz = 0, lb = 0;
+    if (q < Z.m) {
+      const K key = ld_key<K>((const K *)P.mh_keys + Z.mh + q);
+      sz = __ldcg((const long long *)&P.mh_sizes[Z.mh + q]);
+      int64_t a = 0, b = Z.b0;
+      while (a < b) {
+        const int64_t mid = (a + b) >> 1;
+        if (ld_key<K>(B0 + mid) < key) a = mid + 1;
+        else b = mid;
+      }
+      lb = a;
+    }
+    long long tot;
+    const long long pre = block_excl_scan<long long>(sz, sh, tot);
+    if (q < Z.m) P.mh_start[Z.mh + q] = Z.zs + lb + pre;
+    __syncthreads();
+  }
+}
+
+template <typename K, bool HV>
+__device__ void phase_merge(const Params &P, int level, unsigned char *smem) {
+  Ctl *c = P.ctl;
+  const int64_t z0 = min(ld_cg64(&c->lvl_zone[level]), (long long)P.mhmax);
+  const int64_t z1 = min(ld_cg64(&c->lvl_zone[level + 1]), (long long)P.mhmax);
+  const int64_t c0 = (int64_t)__ldcg(&c->lvl_chunk[level]);
+  const int64_t c1 = (int64_t)__ldcg(&c->lvl_chunk[level + 1]);
+  Carve cv(smem);
+  long long *hs = cv.take<long long>(HASH_HW / 2 + 1);
+  long long *hz = cv.take<long long>(HASH_HW / 2 + 1);
+  long long *hp = cv.take<long long>(HASH_HW / 2 + 1);
+  long long *sh = cv.take<long long>(NWARP + 1);
+  MZone *Zs = cv.take<MZone>(1);
+  long long my = 0;
+  int64_t curz = -1;
+  for (int64_t ch = c0 + blockIdx.x; ch < c1; ch += gridDim.x) {
+    int64_t a = z0, b = z1 - 1;
+    while (a < b) {
+      const int64_t mid = (a + b + 1) >> 1;
+      if (__ldcg((const long long *)&P.zones[mid].chunk0) <= ch) a = mid;
+      else b = mid - 1;
+    }
+    if (a != curz) {
+      __syncthreads();
+      if (threadIdx.x == 0) *Zs = ldcg_obj(&P.zones[a]);
+      __syncthreads();
+      const int q = threadIdx.x;
+      long long sz = 0;
+      if (q < Zs->m) {
+        sz = __ldcg((const long long *)&P.mh_sizes[Zs->mh + q]);
+        hs[q] = __ldcg((const long long *)&P.mh_start[Zs->mh + q]);
+        hz[q] = sz;
+      }
+      long long tot;
+      const long long pre = block_excl_scan<long long>(sz, sh, tot);
+      if (q < Zs->m) hp[q] = pre;
+      __syncthreads();
+      curz = a;
+    }
+    const MZone &Z = *Zs;
+    const int ib = Z.obuf ^ 1;
+    const K *kin = (const K *)P.keys[ib];
+    K *kout = (K *)P.keys[Z.obuf];
+    const K *vin = HV ? (const K *)P.vals[ib] : nullptr;
+    K *vout = HV ? (K *)P.vals[Z.obuf] : nullptr;
+    const int64_t o0 = Z.zs + (ch - Z.chunk0) * MERGE_CHUNK;
+    const int64_t o1 = o0 + MERGE_CHUNK < Z.ze ? o0 + MERGE_CHUNK : Z.ze;
+    for (int64_t pp = o0 + threadIdx.x; pp < o1; pp += NT) {
+      int lo = 0, hi = Z.m;  // count of heavy buckets starting at or before pp
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (hs[mid] <= pp) lo = mid + 1;
+        else hi = mid;
+      }
+      const int i = lo - 1;
+      int64_t from;
+      if (i >= 0 && pp < hs[i] + hz[i]) {
+        from = Z.zs + Z.b0 + hp[i] + (pp - hs[i]);
+      } else {
+        const int64_t before = i >= 0 ? hp[i] + hz[i] : 0;
+        from = pp - before;
+      }
+      if (from < Z.zs || from >= Z.ze) {
+        latch(P, ERR_INTERNAL);
+        continue;
+      }
+      kout[pp] = ld_key<K>(kin + from);
+      if constexpr (HV) vout[pp] = ld_key<K>(vin + from);
+    }
+    my += o1 - o0;
+  }
+  if (threadIdx.x == 0 && my) atomic_add_ll(&c->st_merge_records, my);
+}
+
+// ------------------------------------------------------------------ kernel
+__device__ __forceinline__ void tick(const Params &P, int kind) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    const unsigned long long now = gtimer();
+    P.ctl->t_phase[kind] += now - P.ctl->t_last;
+    P.ctl->t_last = now;
+  }
+}
+
+template <typename K, bool HV>
+__global__ void __launch_bounds__(NT, 2) dtsort_kernel(const Params P) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  Ctl *c = P.ctl;
+  if (blockIdx.x == 0 && threadIdx.x == 0) c->t_last = gtimer();
+  const unsigned long long tbeg = gtimer();
+  phase_seed<K, HV>(P);
+  grid_sync(P);
+  tick(P, PH_SETUP);
+  int level = 0;
+  for (; level < MAXLEV; ++level) {
+    const int p = level & 1;
+    const long long nseg = ld_cg64(&c->nseg[p]);
+    if (level > 0 && nseg == 0) break;
+    if (*(volatile int *)&c->err_snap) break;
+    if (blockIdx.x == 0) phase_setup<K, HV>(P, level, smem);
+    grid_sync(P);
+    tick(P, PH_SETUP);
+    if (*(volatile int *)&c->err_snap) break;  // e.g. a table would overflow
+    if (nseg > 0) {
+      phase_sample<K, HV>(P, level, smem);
+      grid_sync(P);
+      tick(P, PH_SAMPLE);
+      phase_hist<K, HV>(P, level, smem);
+      grid_sync(P);
+      tick(P, PH_HIST);
+      phase_scan<K, HV>(P, level, smem);
+      grid_sync(P);
+      tick(P, PH_SCAN);
+      phase_scatter<K, HV>(P, level, smem);
+      grid_sync(P);
+      tick(P, PH_SCATTER);
+    }
+    phase_finish<K, HV>(P, level, smem);
+    grid_sync(P);
+    tick(P, PH_FINISH);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    c->nlevels = level;
+    const unsigned long long za = __ldcg(&c->zone_alloc);
+    c->lvl_zone[level] = (long long)(za >> 40);
+    c->lvl_chunk[level] = za & ((1ull << 40) - 1);
+  }
+  grid_sync(P);
+  for (int l = level - 1; l >= 0; --l) {
+    if (*(volatile int *)&c->err_snap) break;
+    if (ld_cg64(&c->lvl_zone[l + 1]) == ld_cg64(&c->lvl_zone[l])) continue;
+    phase_merge_prep<K, HV>(P, l, smem);
+    grid_sync(P);
+    phase_merge<K, HV>(P, l, smem);
+    grid_sync(P);
+    tick(P, PH_MERGE);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    DevStats *d = P.stats;
+    const int L = c->nlevels;
+    d->levels = L;
+    d->status = *(volatile int *)&c->error;
+    for (int l = 0; l < 16; ++l) {
+      d->segments[l] = ld_cg64(&c->st_segments[l]);
+      d->records[l] = ld_cg64(&c->st_records[l]);
+      d->heavy_keys[l] = ld_cg64(&c->st_heavy_keys[l]);
+      d->heavy_records[l] = ld_cg64(&c->st_heavy_records[l]);
+      d->overflow_records[l] = ld_cg64(&c->st_overflow[l]);
+    }
+    d->finisher_tasks = ld_cg64(&c->st_fin_tasks);
+    d->finisher_records = ld_cg64(&c->st_fin_records);
+    d->copy_records = ld_cg64(&c->st_copy_records);
+    d->merge_zones = (int64_t)(__ldcg(&c->zone_alloc) >> 40);
+    d->merge_records = ld_cg64(&c->st_merge_records);
+    d->learned_fixup_records = 0;
+    d->learned_fixup_steps = 0;
+    d->learned_cv = 0;
+    d->learned_mom = 0;
+    for (int k = 0; k < 7; ++k) d->phase_ms[k] = (double)c->t_phase[k] * 1e-6;
+    d->phase_ms[7] = (double)(gtimer() - tbeg) * 1e-6;
+  }
+}
+
+// ---------------------------------------------------- sampler diagnostic
+// Alg. 2 step 1 on one subproblem, exactly as phase_sample draws it.
+template <typename K>
+__global__ void __launch_bounds__(NT) sample_debug_kernel(const K *keys, int64_t start,
+                                                          int64_t size, int hi, uint64_t seed,
+                                                          int64_t m, int64_t L, uint64_t *heavy_out,
+                                                          int64_t *nheavy_out, uint64_t *max_out) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  Carve cv(smem);
+  K *Ssm = cv.take<K>(SMAX);
+  long long *sh = cv.take<long long>(NWARP + 1);
+  int M = 1;
+  while (M < m) M <<= 1;
+  const uint64_t st =
+      seed ^ (uint64_t)start ^ ((uint64_t)size * 0x9E3779B97F4A7C15ull) ^ ((uint64_t)hi << 57);
+  for (int k = threadIdx.x; k < M; k += NT) {
+    if (k < m) {
+      const int64_t pos = start + (int64_t)(sm64_at(st, (uint64_t)k) % (uint64_t)size);
+      Ssm[k] = ld_key<K>(keys + pos);
+    } else {
+      Ssm[k] = (K)~(K)0;
+    }
+  }
+  __syncthreads();
+  for (int kk = 2; kk <= M; kk <<= 1) {
+    for (int j = kk >> 1; j > 0; j >>= 1) {
+      for (int i = threadIdx.x; i < M; i += NT) {
+        const int ixj = i ^ j;
+        if (ixj > i) {
+          const K a = Ssm[i], b = Ssm[ixj];
+          const bool up = (i & kk) == 0;
+          if ((a > b) == up) {
+            Ssm[i] = b;
+            Ssm[ixj] = a;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  const int64_t nsub = m / L;
+  long long carry = 0;
+  for (int64_t base = 0; base < nsub; base += NT) {
+    const int64_t j = base + threadIdx.x;
+    int first = 0;
+    K a = 0;
+    if (j + 1 < nsub) {
+      a = Ssm[(j + 1) * L - 1];
+      const K b = Ssm[(j + 2) * L - 1];
+      first = (a == b) && (j == 0 || Ssm[j * L - 1] != a);
+    }
+    long long tot;
+    const long long o = block_excl_scan<long long>(first, sh, tot) + carry;
+    if (first) heavy_out[o] = (uint64_t)a;
+    carry += tot;
+  }
+  if (threadIdx.x == 0) {
+    *nheavy_out = carry;
+    *max_out = (uint64_t)Ssm[m - 1];
+  }
+}
+
+}  // namespace dts

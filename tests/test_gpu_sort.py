@@ -1,0 +1,285 @@
+"""GPU parity: the CUDA sort through the C-ABI against the CPU oracle, bit for
+bit (a stable sort's output is unique, so there is no tolerance)."""
+import numpy as np
+import pytest
+
+import gen
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+import gpu_util  # noqa: E402
+import paper_2401_00710_gb300 as dts  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def G():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    g = gpu_util.GpuSort(torch)
+    yield g
+    g.reset_options()
+    g.ws = None
+    g.close()
+
+
+@pytest.fixture(autouse=True)
+def _defaults(G):
+    G.reset_options()
+    yield
+    G.reset_options()
+
+
+def check(G, keys, vals=None, offsets=None):
+    gk, gv = G.sort(keys, vals, offsets)
+    if offsets is None:
+        ek, ev = oracle.stable_sort(keys, vals)
+    else:
+        ek, ev = oracle.stable_sort_segmented(keys, vals, offsets)
+    gpu_util.assert_same(gk, gv, ek, ev)
+    return G.stats()
+
+
+# ------------------------------------------------------------ configurations
+def test_config_small_uniform_u32_kv(G):
+    # 10^6 uint32 keys uniform, values = original index
+    n = 1_000_000
+    keys = gen.family("uniform", n, np.uint32, seed=1)
+    vals = gen.iota(n, np.uint32)
+    st = check(G, keys, vals)
+    assert st["status"] == 0
+    assert st["heavy_keys"][0] == 0
+
+
+U32_NAMES = sorted(gen.U32_FAMILIES)
+
+
+@pytest.mark.parametrize("name", U32_NAMES)
+def test_u32_kv_families(G, name):
+    n = 3_000_017
+    keys = gen.family(name, n, np.uint32, seed=2)
+    vals = gen.iota(n, np.uint32)
+    check(G, keys, vals)
+
+
+@pytest.mark.parametrize("name", ["uniform", "zipf1.2", "distinct10", "bitexp"])
+def test_u32_key_only(G, name):
+    n = 2_500_001
+    keys = gen.family(name, n, np.uint32, seed=3)
+    check(G, keys)
+
+
+@pytest.mark.parametrize("name", sorted(gen.U64_FAMILIES))
+def test_u64_kv_families(G, name):
+    n = 1_500_007
+    keys = gen.family(name, n, np.uint64, seed=4)
+    vals = gen.iota(n, np.uint64)
+    check(G, keys, vals)
+
+
+@pytest.mark.parametrize("name", ["uniform", "heavymix", "zipf1.2hash"])
+def test_u64_key_only(G, name):
+    n = 1_200_003
+    keys = gen.family(name, n, np.uint64, seed=5)
+    check(G, keys)
+
+
+# -------------------------------------------------------------- edge cases
+EDGE_N = [1, 2, 3, 31, 32, 33, 511, 513, 3071, 3072, 3073, 4095, 4096, 4097,
+          6143, 6144, 6145, 8191, 8192, 8193, 12288, 12289, 16391, 100_003]
+
+
+@pytest.mark.parametrize("n", EDGE_N)
+@pytest.mark.parametrize("dtype", [np.uint32, np.uint64])
+def test_edge_sizes_kv(G, n, dtype):
+    keys = gen.family("uniform", n, dtype, seed=n)
+    keys[: n // 3] = keys[0]  # a run of duplicates as well
+    vals = gen.iota(n, dtype)
+    check(G, keys, vals)
+
+
+def test_n_zero_is_noop(G):
+    keys = np.zeros(0, dtype=np.uint32)
+    st = G.launch(None, None, 0, dts.DTSORT_OP_U32_KV)
+    assert st == dts.DTSORT_OK
+    assert G.device_status() == dts.DTSORT_OK
+
+
+@pytest.mark.parametrize("dtype", [np.uint32, np.uint64])
+def test_special_inputs(G, dtype):
+    top = np.iinfo(dtype).max
+    n = 200_000
+    vals = gen.iota(n, dtype)
+    for keys in (np.full(n, 7, dtype=dtype),                       # all equal
+                 np.full(n, top, dtype=dtype),                     # all max
+                 np.arange(n, dtype=dtype),                        # sorted
+                 np.arange(n, dtype=dtype)[::-1].copy(),           # reversed
+                 np.tile(np.array([top, 0, 1, top - 1], dtype=dtype), n // 4),
+                 (np.arange(n, dtype=dtype) % 2) * top):           # two values
+        check(G, keys, vals)
+
+
+def test_narrow_key_ranges(G):
+    # keys confined to a narrow range high up: exercises the overflow bucket
+    # and the skipped leading bits
+    n = 400_000
+    base = np.uint32(0xF0000000)
+    keys = (gen.family("uniform", n, np.uint32, seed=8) % 5000 + base).astype(np.uint32)
+    check(G, keys, gen.iota(n, np.uint32))
+    keys64 = (gen.family("uniform", n, np.uint64, seed=9) % 70000 +
+              np.uint64(1 << 63)).astype(np.uint64)
+    check(G, keys64, gen.iota(n, np.uint64))
+
+
+def test_overflow_bucket_outliers(G):
+    # small keys plus rare huge outliers that a sample can miss
+    n = 600_000
+    keys = (gen.family("uniform", n, np.uint32, seed=10) % 100_000).astype(np.uint32)
+    keys[::99_991] = 0xFFFFFFF0
+    check(G, keys, gen.iota(n, np.uint32))
+
+
+# ---------------------------------------------------------------- options
+@pytest.mark.parametrize("opts", [dict(heavy_detection=-1), dict(gamma_max=2),
+                                  dict(gamma_max=5, finisher_capacity=700),
+                                  dict(finisher_capacity=64),
+                                  dict(seed=12345, sample_log_factor=3)])
+def test_options_do_not_change_output(G, opts):
+    n = 700_001
+    for name in ("zipf1.2", "uniform", "bitexp"):
+        keys = gen.family(name, n, np.uint32, seed=11)
+        vals = gen.iota(n, np.uint32)
+        G.set_options(**opts)
+        check(G, keys, vals)
+
+
+# --------------------------------------------------------------- segmented
+@pytest.mark.parametrize("dtype", [np.uint32, np.uint64])
+def test_segmented(G, dtype):
+    rs = np.random.RandomState(12)
+    sizes = np.concatenate([rs.randint(0, 3, 40), rs.randint(0, 5000, 100),
+                            rs.randint(5000, 200_000, 12)])
+    rs.shuffle(sizes)
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    n = int(off[-1])
+    keys = gen.family("zipf1.2hash", n, dtype, seed=13)
+    vals = np.zeros(n, dtype=dtype)
+    for s in range(len(sizes)):
+        vals[off[s]:off[s + 1]] = np.arange(sizes[s], dtype=dtype)
+    check(G, keys, vals, off)
+    check(G, keys, None, off)
+
+
+def test_segmented_bad_offsets_reported(G):
+    keys = gen.family("uniform", 1000, np.uint32, seed=1)
+    off = np.array([0, 600, 400, 1000], dtype=np.int64)  # decreasing
+    k = gpu_util.to_dev(keys, torch, G.dev)
+    o = torch.from_numpy(off).to(G.dev)
+    st = G.launch(k, None, 1000, dts.DTSORT_OP_U32, o, 3)
+    assert st == dts.DTSORT_OK
+    assert G.device_status() == dts.DTSORT_ERR_INVALID_ARG
+
+
+# ----------------------------------------------------- method structure
+def test_ten_distinct_keys_are_all_heavy_at_the_root(G):
+    # Thm 3.5: with few distinct keys every key is heavy at the root, and
+    # nothing is distributed again
+    n = 4_000_000
+    keys = gen.family("distinct10", n, np.uint32, seed=1)
+    st = check(G, keys, gen.iota(n, np.uint32))
+    assert st["heavy_keys"][0] == 10
+    assert st["records"][1] == 0
+    assert st["heavy_records"][0] == n
+
+
+def test_uniform_has_no_heavy_keys_and_two_levels(G):
+    n = 2_000_000
+    keys = gen.family("uniform", n, np.uint32, seed=1)
+    st = check(G, keys, gen.iota(n, np.uint32))
+    assert sum(st["heavy_keys"]) == 0
+    assert st["merge_zones"] == 0
+    assert st["finisher_records"] == n
+
+
+def test_zipf_detects_heavy_and_merges(G):
+    n = 3_000_000
+    keys = gen.family("zipf1.2", n, np.uint32, seed=1)
+    st = check(G, keys, gen.iota(n, np.uint32))
+    assert st["heavy_keys"][0] > 0
+    assert st["merge_zones"] > 0
+    # DTMerge writes every record of a merged zone exactly once per zone
+    assert st["merge_records"] >= st["heavy_records"][0]
+
+
+def test_deterministic(G):
+    n = 1_000_000
+    keys = gen.family("zipf1.0", n, np.uint32, seed=21)
+    vals = gen.iota(n, np.uint32)
+    G.sort(keys, vals)
+    a = G.stats()
+    G.sort(keys, vals)
+    b = G.stats()
+    for k in ("levels", "segments", "records", "heavy_keys", "heavy_records",
+              "overflow_records", "finisher_tasks", "merge_zones", "merge_records"):
+        assert a[k] == b[k], k
+
+
+@pytest.mark.parametrize("dtype", [np.uint32, np.uint64])
+def test_sampler_matches_oracle(G, dtype):
+    n = 2_000_000
+    keys = gen.family("zipf1.2" if dtype == np.uint32 else "heavymix", n, dtype, seed=3)
+    keys[1000:300_000] = keys[5]
+    d = gpu_util.to_dev(keys, torch, G.dev)
+    heavy = torch.zeros(8192, dtype=torch.int64, device=G.dev)
+    nh = torch.zeros(1, dtype=torch.int64, device=G.dev)
+    mx = torch.zeros(1, dtype=torch.int64, device=G.dev)
+    s = torch.cuda.current_stream(G.dev).cuda_stream
+    for (start, size, hi, seed, count, L) in [(0, n, 8 * keys.itemsize, 1, 7680, 21),
+                                              (12345, 999_999, 20, 77, 8192, 17),
+                                              (5, 300_000, 3, 2, 1000, 3),
+                                              (0, 10, 32, 9, 4096, 1)]:
+        st = dts.dtsort_debug_sample(G.h, d.data_ptr(), keys.itemsize, start, size, hi,
+                                     seed, count, L, heavy.data_ptr(), nh.data_ptr(),
+                                     mx.data_ptr(), s)
+        assert st == dts.DTSORT_OK
+        torch.cuda.synchronize()
+        got_n = int(nh.item())
+        got = heavy[:got_n].cpu().numpy().view(np.uint64)
+        exp, exp_max = oracle.sample_heavy(keys, seed, start, size, hi, count, L)
+        np.testing.assert_array_equal(got, exp)
+        assert int(mx.cpu().numpy().view(np.uint64)[0]) == exp_max
+
+
+# ------------------------------------------------------------ error paths
+def test_argument_checks(G):
+    n = 1000
+    k = torch.zeros(n, dtype=torch.int32, device=G.dev)
+    ws = G.workspace(dts.DTSORT_OP_U32, n)
+    s = torch.cuda.current_stream(G.dev).cuda_stream
+    assert dts.dtsort_u32(G.h, k.data_ptr(), -1, ws.data_ptr(), ws.numel(), s) == \
+        dts.DTSORT_ERR_INVALID_ARG
+    assert dts.dtsort_u32(G.h, None, n, ws.data_ptr(), ws.numel(), s) == \
+        dts.DTSORT_ERR_INVALID_ARG
+    assert dts.dtsort_u32_kv(G.h, k.data_ptr(), None, n, ws.data_ptr(), ws.numel(), s) == \
+        dts.DTSORT_ERR_INVALID_ARG
+    assert dts.dtsort_u32(G.h, k.data_ptr(), n, ws.data_ptr(), 100, s) == \
+        dts.DTSORT_ERR_WORKSPACE_TOO_SMALL
+    assert dts.dtsort_u32(G.h, k.data_ptr() + 1, n, ws.data_ptr(), ws.numel(), s) == \
+        dts.DTSORT_ERR_INVALID_ARG
+
+
+def test_bounded_wait_expires_without_hanging(G):
+    # a tile that never publishes its look-back status: the successors' waits
+    # run out, the sort latches DEVICE_TIMEOUT and the context stays usable
+    n = 200_000
+    keys = gen.family("uniform", n, np.uint32, seed=4)
+    vals = gen.iota(n, np.uint32)
+    G.set_options(debug_fault=1, wait_limit_ms=50)
+    k = gpu_util.to_dev(keys, torch, G.dev)
+    v = gpu_util.to_dev(vals, torch, G.dev)
+    assert G.launch(k, v, n, dts.DTSORT_OP_U32_KV) == dts.DTSORT_OK
+    assert G.device_status() == dts.DTSORT_ERR_DEVICE_TIMEOUT
+    G.reset_options()
+    check(G, keys, vals)
