@@ -29,7 +29,8 @@
  *     bounded wait that timed out, an exhausted internal table) are latched
  *     in the handle and read with dtsort_last_device_error().
  *   - No call allocates device memory, except dtsort_create() (a few KB).
- *   - n == 0 is a no-op returning DTSORT_OK.  n < 0, or a NULL pointer where
+ *   - n == 0 is a no-op returning DTSORT_OK; n >= 2^32 returns
+ *     DTSORT_ERR_UNSUPPORTED.  n < 0, or a NULL pointer where
  *     n > 0 needs one, returns DTSORT_ERR_INVALID_ARG.  A workspace smaller
  *     than dtsort_workspace_bytes() returns DTSORT_ERR_WORKSPACE_TOO_SMALL.
  *     Keys/values must be aligned to their own width; the workspace to 256 B.
@@ -97,8 +98,8 @@ typedef struct {
   int32_t wait_limit_ms;     /* bound of every device-side wait (default 2000);
                                 when it expires the sort latches
                                 DTSORT_ERR_DEVICE_TIMEOUT and writes nothing more */
-  int32_t debug_fault;       /* testing only: 1 = the second tile of the first
-                                distribution never publishes its look-back
+  int32_t debug_fault;       /* testing only: 1 = the second look-back chunk of
+                                the first distribution never publishes its
                                 status, so its successors' waits expire */
   int32_t reserved[6];
 } dtsort_options;

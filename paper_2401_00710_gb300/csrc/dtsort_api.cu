@@ -20,8 +20,8 @@ constexpr int kOps = 4;
 
 struct Layout {
   size_t tkeys, tvals, ctl, segs0, segs1, info, bcount, bstart, lid, heavy, hashk, hashid,
-      status, tasks, zones, mhk, mhs, mhst, total;
-  int64_t maxseg, bmax, hmax, zmax, hashmax, swords, tmax, mhmax;
+      cmat, status, tasks, zones, mhk, mhs, mhst, total;
+  int64_t maxseg, bmax, hmax, zmax, hashmax, cwords, swords, tmax, mhmax;
   int cap;
   int64_t target;
 };
@@ -83,7 +83,8 @@ size_t up(size_t x) { return (x + 255) & ~(size_t)255; }
 // Upper bounds of every device table for n records in nsegs arrays.  The
 // digit width rule gives 2^gamma < 2*size/target for every subproblem
 // (size > cap > target), which bounds the per-level sums below.
-Layout make_layout(int kb, int vb, int64_t n, int64_t nsegs, const Opts &o, int tile) {
+Layout make_layout(int kb, int vb, int64_t n, int64_t nsegs, const Opts &o,
+                   const KernelShape &ks) {
   Layout L{};
   L.cap = o.cap;
   L.target = std::max<int64_t>(16, (int64_t)o.cap * 7 / 10);
@@ -93,7 +94,10 @@ Layout make_layout(int kb, int vb, int64_t n, int64_t nsegs, const Opts &o, int 
   L.hmax = nt + L.maxseg + 1024;
   L.zmax = 2 * nt + 2 * L.maxseg + 1024;
   L.hashmax = 2 * nt + L.maxseg + 1024;
-  L.swords = (int64_t)dts::NB_HW * (n / tile + 1) + L.bmax;
+  // count matrix: one row of <= NB_HW words per block of every subproblem;
+  // look-back status: one row per chunk of ks.ch rows
+  L.cwords = (int64_t)dts::NB_HW * (n / ks.blk + 1) + L.bmax;
+  L.swords = (int64_t)dts::NB_HW * (n / ((int64_t)ks.blk * ks.ch) + 1) + L.bmax;
   L.tmax = 2 * L.bmax + 2 * (n / dts::COPY_CHUNK + 1) + nsegs + 4096;
   L.mhmax = 4 * L.hmax + 4096;
   size_t off = 0;
@@ -114,6 +118,7 @@ Layout make_layout(int kb, int vb, int64_t n, int64_t nsegs, const Opts &o, int 
   L.heavy = take((size_t)kb * L.hmax);
   L.hashk = take((size_t)kb * L.hashmax);
   L.hashid = take(2 * (size_t)L.hashmax);
+  L.cmat = take(4 * (size_t)L.cwords);
   L.status = take(8 * (size_t)L.swords);
   L.tasks = take(sizeof(dts::Task) * (size_t)L.tmax);
   L.zones = take(sizeof(dts::MZone) * (size_t)L.mhmax);
@@ -134,6 +139,7 @@ dtsort_status run_sort(dtsort_handle h, int op, void *keys, void *vals, const in
   if (n < 0 || nsegs < 0) return DTSORT_ERR_INVALID_ARG;
   if (offsets && nsegs == 0) return n == 0 ? DTSORT_OK : DTSORT_ERR_INVALID_ARG;
   if (n == 0) return DTSORT_OK;
+  if (n >= ((int64_t)1 << 32)) return DTSORT_ERR_UNSUPPORTED;  // 32-bit block offsets
   if (!keys || (has_vals(op) && !vals) || !ws) return DTSORT_ERR_INVALID_ARG;
   const int kb = key_bytes(op), vb = has_vals(op) ? kb : 0;
   if (((uintptr_t)keys % kb) || (vals && ((uintptr_t)vals % kb)) || ((uintptr_t)ws % 256))
@@ -146,7 +152,7 @@ dtsort_status run_sort(dtsort_handle h, int op, void *keys, void *vals, const in
   if (e != cudaSuccess) return DTSORT_ERR_CUDA;
   if (ks->blocks_per_sm < 1) return DTSORT_ERR_UNSUPPORTED;
   const Opts o = effective(h->opt, *ks);
-  const Layout L = make_layout(kb, vb, n, offsets ? nsegs : 1, o, ks->tile);
+  const Layout L = make_layout(kb, vb, n, offsets ? nsegs : 1, o, *ks);
   if (ws_bytes < L.total) return DTSORT_ERR_WORKSPACE_TOO_SMALL;
   char *w = (char *)ws;
   Params P{};
@@ -176,6 +182,7 @@ dtsort_status run_sort(dtsort_handle h, int op, void *keys, void *vals, const in
   P.heavy = w + L.heavy;
   P.hash_keys = w + L.hashk;
   P.hash_ids = (uint16_t *)(w + L.hashid);
+  P.cmat = (unsigned *)(w + L.cmat);
   P.status = (unsigned long long *)(w + L.status);
   P.tasks = (dts::Task *)(w + L.tasks);
   P.zones = (dts::MZone *)(w + L.zones);
@@ -187,6 +194,7 @@ dtsort_status run_sort(dtsort_handle h, int op, void *keys, void *vals, const in
   P.hmax = L.hmax;
   P.zmax = L.zmax;
   P.hashmax = L.hashmax;
+  P.cwords = L.cwords;
   P.swords = L.swords;
   P.tmax = L.tmax;
   P.mhmax = L.mhmax;
@@ -309,7 +317,7 @@ dtsort_status dtsort_workspace_bytes(dtsort_handle h, dtsort_op op, int64_t n,
   if (get_shape(h, op, &ks) != cudaSuccess) return DTSORT_ERR_CUDA;
   const Opts o = effective(h->opt, *ks);
   const int kb = key_bytes(op), vb = has_vals(op) ? kb : 0;
-  *bytes = make_layout(kb, vb, n, num_segments > 0 ? num_segments : 1, o, ks->tile).total;
+  *bytes = make_layout(kb, vb, n, num_segments > 0 ? num_segments : 1, o, *ks).total;
   return DTSORT_OK;
 }
 

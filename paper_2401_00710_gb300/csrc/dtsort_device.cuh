@@ -50,19 +50,23 @@ struct Seg {
   uint8_t pad[3];
 };
 
-// Per subproblem of the current level, filled by setup + sample.
+// Per subproblem of the current level, filled by setup + sample.  The
+// subproblem is cut into blocks of BLK records (rows of its count matrix) and
+// the rows into look-back chunks of CH rows.
 struct SegInfo {
   int32_t gamma;    // planned digit width
   int32_t lo, t;    // MSD zone digit = key bits [lo, t)
   int32_t nheavy;
   int32_t nb;       // 2^(t-lo) + nheavy + 1 (overflow last)
   int32_t hbits;    // log2 hash capacity (0: no heavy keys)
-  int64_t ntiles, tile0;
-  int64_t boff;     // bucket arrays (counts / starts)
+  int64_t nblk, blk0;  // blocks, first global block index
+  int64_t nchk, chk0;  // chunks, first global chunk index
+  int64_t boff;     // bucket arrays (totals / starts)
   int64_t hoff;     // heavy keys, sorted
   int64_t zoff;     // light table L: 2^(t-lo)+1 entries
   int64_t hashoff;  // heavy hash table H
-  int64_t soff;     // look-back status words: ntiles x nb
+  int64_t coff;     // count matrix, u32, nblk x nb (becomes block offsets)
+  int64_t soff;     // chunk look-back status words, nchk x nb
   int64_t mhoff;    // persistent heavy store reservation (for merges)
 };
 
@@ -88,7 +92,7 @@ struct Ctl {
   int err_snap;   // error as of the last grid barrier: every CTA decides alike
   int pad_;
   long long nseg[2];
-  long long tile_ctr, ntiles;
+  long long chunk_ctr, nblocks, nchunks;
   long long ntasks, task_ctr;
   unsigned long long zone_alloc;  // (zones << 40) | chunks
   long long mh_alloc;
@@ -138,12 +142,13 @@ struct Params {
   void *heavy;
   void *hash_keys;
   uint16_t *hash_ids;
+  unsigned *cmat;
   unsigned long long *status;
   Task *tasks;
   MZone *zones;
   void *mh_keys;
   int64_t *mh_sizes, *mh_start;
-  int64_t maxseg, bmax, hmax, zmax, hashmax, swords, tmax, mhmax;
+  int64_t maxseg, bmax, hmax, zmax, hashmax, cwords, swords, tmax, mhmax;
   int *dev_status;
   DevStats *stats;
 };
@@ -274,12 +279,42 @@ __device__ __forceinline__ T block_excl_scan(T v, T *sh, T &total) {
 }
 
 // Rank of this lane's item among the warp's items with the same bucket that
-// come earlier in (round, lane) order; wc is the warp's counter row.
-__device__ __forceinline__ unsigned warp_rank(unsigned b, uint16_t *wc) {
+// come earlier in (round, lane) order; wc is the warp's counter row.  The
+// lanes holding the same bucket are found with one ballot per bit of the
+// bucket id (nbits bits), whose cost does not grow with the number of
+// distinct buckets in the warp.
+__device__ __forceinline__ unsigned lanemask_lt() {
+  unsigned m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+__device__ __forceinline__ unsigned warp_peers(unsigned b, int nbits) {
+  unsigned peers = 0xffffffffu;
+  for (int k = 0; k < nbits; ++k) {
+    const unsigned bit = (b >> k) & 1u;
+    const unsigned bal = __ballot_sync(0xffffffffu, bit);
+    peers &= bit ? bal : ~bal;
+  }
+  return peers;
+}
+
+template <int NBITS>
+__device__ __forceinline__ unsigned warp_peers_fixed(unsigned b) {
+  unsigned peers = 0xffffffffu;
+#pragma unroll
+  for (int k = 0; k < NBITS; ++k) {
+    const unsigned bit = (b >> k) & 1u;
+    const unsigned bal = __ballot_sync(0xffffffffu, bit);
+    peers &= bit ? bal : ~bal;
+  }
+  return peers;
+}
+
+__device__ __forceinline__ unsigned warp_rank_peers(unsigned b, unsigned peers, uint16_t *wc) {
   const unsigned lane = threadIdx.x & 31;
-  unsigned peers = __match_any_sync(0xffffffffu, b);
-  unsigned leader = __ffs(peers) - 1;
-  unsigned before = __popc(peers & ((1u << lane) - 1u));
+  const unsigned leader = __ffs(peers) - 1;
+  const unsigned before = __popc(peers & lanemask_lt());
   unsigned old = 0;
   if (lane == leader) {
     old = wc[b];
@@ -364,12 +399,23 @@ __device__ void load_tables(const Params &P, int seg, int level, SegTables<K> &T
   __syncthreads();
 }
 
-// index of the segment owning global tile t (tile0 increasing)
-__device__ __forceinline__ int find_tile_seg(const Params &P, int64_t nseg, int64_t t) {
+// index of the subproblem owning global block r (blk0 increasing)
+__device__ __forceinline__ int find_blk_seg(const Params &P, int64_t nseg, int64_t r) {
   int64_t lo = 0, hi = nseg - 1;
   while (lo < hi) {
     int64_t mid = (lo + hi + 1) >> 1;
-    if (__ldcg((const long long *)&P.info[mid].tile0) <= t) lo = mid;
+    if (__ldcg((const long long *)&P.info[mid].blk0) <= r) lo = mid;
+    else hi = mid - 1;
+  }
+  return (int)lo;
+}
+
+// index of the subproblem owning global look-back chunk c (chk0 increasing)
+__device__ __forceinline__ int find_chk_seg(const Params &P, int64_t nseg, int64_t c) {
+  int64_t lo = 0, hi = nseg - 1;
+  while (lo < hi) {
+    int64_t mid = (lo + hi + 1) >> 1;
+    if (__ldcg((const long long *)&P.info[mid].chk0) <= c) lo = mid;
     else hi = mid - 1;
   }
   return (int)lo;

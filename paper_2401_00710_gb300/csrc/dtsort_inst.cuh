@@ -20,6 +20,8 @@ cudaError_t DTS_CAT(shape_, DTS_NAME)(KernelShape *out) {
   if (e != cudaSuccess) return e;
   out->fin_cap = S::FIN_CAP;
   out->tile = S::TILE;
+  out->blk = S::BLK;
+  out->ch = S::CH;
   out->smem = smem;
   out->blocks_per_sm = nb;
   return cudaSuccess;

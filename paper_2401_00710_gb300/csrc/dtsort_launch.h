@@ -13,6 +13,8 @@ namespace dts {
 struct KernelShape {
   int fin_cap;
   int tile;
+  int blk;   // records per count-matrix row
+  int ch;    // rows per look-back chunk
   size_t smem;
   int blocks_per_sm;
 };

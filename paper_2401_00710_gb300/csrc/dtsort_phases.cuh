@@ -16,6 +16,9 @@ struct Shape {
   static constexpr int FIN_CAP = FIN_BYTES / (2 * (KB + VB));
   static constexpr int FIN_IT = FIN_CAP / NT;           // base-case items / thread
   static constexpr int STAGE = TILE * KB;               // scatter staging (keys or values)
+  static constexpr int BLK_TILES = 4;                   // tiles per count-matrix row
+  static constexpr int BLK = BLK_TILES * TILE;          // records per block
+  static constexpr int CH = 32;                         // rows per look-back chunk
 };
 
 struct Carve {
@@ -40,7 +43,7 @@ constexpr size_t smem_bytes() {
   sc += 16 + (size_t)S::STAGE;                     // key / value staging
   sc += 16 + 2 * (size_t)S::TILE;                  // bucket of each staged slot
   sc += 16 + 2 * (size_t)NWARP * NB_PAD;           // warp counters
-  sc += 16 + 4 * NB_PAD * 2 + 16 + 8 * NB_PAD;     // tile counts/offsets, bases
+  sc += 16 + 4 * NB_PAD * 2 + 16 + 16 * NB_PAD;    // tile counts/offsets, bases
   sc += 16 + 8 * (NWARP + 1) + 256;
   // base case
   size_t fin = 0;
@@ -144,28 +147,33 @@ __device__ void phase_setup(const Params &P, int level, unsigned char *smem) {
   const int p = level & 1;
   const int64_t nseg = min(ld_cg64(&c->nseg[p]), (long long)P.maxseg);
   long long *sh = (long long *)smem;  // NWARP+1 scratch
-  int64_t cr_tiles = 0, cr_b = 0, cr_h = 0, cr_z = 0, cr_hash = 0, cr_st = 0, cr_rec = 0;
+  int64_t cr_blk = 0, cr_chk = 0, cr_b = 0, cr_h = 0, cr_z = 0, cr_hash = 0, cr_c = 0,
+          cr_st = 0, cr_rec = 0;
   for (int64_t base = 0; base < nseg; base += NT) {
     const int64_t i = base + threadIdx.x;
-    int64_t tiles = 0, nbm = 0, hm = 0, zm = 0, hsm = 0, stm = 0, sz = 0;
+    int64_t nblk = 0, nchk = 0, nbm = 0, hm = 0, zm = 0, hsm = 0, cm = 0, stm = 0, sz = 0;
     int g = 0;
     if (i < nseg) {
       const Seg s = ldcg_obj(&P.segs[p][i]);
       sz = s.size;
       g = plan_gamma(s.size, P.target, P.gamma_max);
-      tiles = (s.size + S::TILE - 1) / S::TILE;
+      nblk = (s.size + S::BLK - 1) / S::BLK;
+      nchk = (nblk + S::CH - 1) / S::CH;
       nbm = (1 << g) + (1 << (g - 1)) + 1;
       hm = 1 << (g - 1);
       zm = (1 << g) + 1;
       hsm = 1 << g;
-      stm = tiles * nbm;
+      cm = nblk * nbm;
+      stm = nchk * nbm;
     }
     long long tot;
-    const int64_t o_t = block_excl_scan<long long>(tiles, sh, tot) + cr_tiles; cr_tiles += tot;
+    const int64_t o_blk = block_excl_scan<long long>(nblk, sh, tot) + cr_blk; cr_blk += tot;
+    const int64_t o_chk = block_excl_scan<long long>(nchk, sh, tot) + cr_chk; cr_chk += tot;
     const int64_t o_b = block_excl_scan<long long>(nbm, sh, tot) + cr_b; cr_b += tot;
     const int64_t o_h = block_excl_scan<long long>(hm, sh, tot) + cr_h; cr_h += tot;
     const int64_t o_z = block_excl_scan<long long>(zm, sh, tot) + cr_z; cr_z += tot;
     const int64_t o_hs = block_excl_scan<long long>(hsm, sh, tot) + cr_hash; cr_hash += tot;
+    const int64_t o_c = block_excl_scan<long long>(cm, sh, tot) + cr_c; cr_c += tot;
     const int64_t o_s = block_excl_scan<long long>(stm, sh, tot) + cr_st; cr_st += tot;
     block_excl_scan<long long>(sz, sh, tot); cr_rec += tot;
     if (i < nseg) {
@@ -175,12 +183,15 @@ __device__ void phase_setup(const Params &P, int level, unsigned char *smem) {
       I.nheavy = 0;
       I.nb = 0;
       I.hbits = 0;
-      I.ntiles = tiles;
-      I.tile0 = o_t;
+      I.nblk = nblk;
+      I.blk0 = o_blk;
+      I.nchk = nchk;
+      I.chk0 = o_chk;
       I.boff = o_b;
       I.hoff = o_h;
       I.zoff = o_z;
       I.hashoff = o_hs;
+      I.coff = o_c;
       I.soff = o_s;
       I.mhoff = 0;
       P.info[i] = I;
@@ -188,11 +199,12 @@ __device__ void phase_setup(const Params &P, int level, unsigned char *smem) {
   }
   if (threadIdx.x == 0) {
     if (cr_b > P.bmax || cr_h > P.hmax || cr_z > P.zmax || cr_hash > P.hashmax ||
-        cr_st > P.swords) {
+        cr_c > P.cwords || cr_st > P.swords) {
       latch(P, ERR_INTERNAL);
     }
-    c->ntiles = cr_tiles;
-    c->tile_ctr = 0;
+    c->nblocks = cr_blk;
+    c->nchunks = cr_chk;
+    c->chunk_ctr = 0;
     c->task_ctr = 0;
     c->merge_ctr = 0;
     c->nseg[p ^ 1] = 0;
@@ -352,13 +364,15 @@ __device__ void phase_sample(const Params &P, int level, unsigned char *smem) {
 }
 
 // ------------------------------------------------------------- histogram
+// Row r of a subproblem's count matrix = bucket counts of its block r (the
+// blocked counting sort of App. B); blocks are split evenly over the CTAs.
 template <typename K, bool HV>
 __device__ void phase_hist(const Params &P, int level, unsigned char *smem) {
   using S = Shape<K, HV>;
   Ctl *c = P.ctl;
   const int64_t nseg = min(ld_cg64(&c->nseg[level & 1]), (long long)P.maxseg);
-  const int64_t ntiles = ld_cg64(&c->ntiles);
-  if (ntiles == 0) return;
+  const int64_t nblocks = ld_cg64(&c->nblocks);
+  if (nblocks == 0) return;
   const K *src = (const K *)P.keys[level & 1];
   Carve cv(smem);
   SegTables<K> &T = *cv.take<SegTables<K>>(1);
@@ -367,42 +381,122 @@ __device__ void phase_hist(const Params &P, int level, unsigned char *smem) {
   uint16_t *hid_s = cv.take<uint16_t>(HASH_HW);
   unsigned *cnt = cv.take<unsigned>(NB_PAD);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int64_t t0 = ntiles * blockIdx.x / gridDim.x;
-  const int64_t t1 = ntiles * (blockIdx.x + 1) / gridDim.x;
+  const int64_t r0 = nblocks * blockIdx.x / gridDim.x;
+  const int64_t r1 = nblocks * (blockIdx.x + 1) / gridDim.x;
   int cur = -1;
-  auto flush = [&]() {
-    __syncthreads();
-    for (int b = threadIdx.x; b < T.info.nb; b += NT)
-      if (cnt[b]) atomicAdd((unsigned long long *)&P.bcount[T.info.boff + b],
-                            (unsigned long long)cnt[b]);
-    __syncthreads();
-  };
-  for (int64_t t = t0; t < t1; ++t) {
+  for (int64_t r = r0; r < r1; ++r) {
     int s = cur;
-    if (cur < 0 || t >= T.info.tile0 + T.info.ntiles) s = find_tile_seg(P, nseg, t);
+    if (cur < 0 || r >= T.info.blk0 + T.info.nblk) s = find_blk_seg(P, nseg, r);
     if (s != cur) {
-      if (cur >= 0) flush();
       load_tables<K>(P, s, level, T, lid_s, hk_s, hid_s);
-      for (int b = threadIdx.x; b < NB_PAD; b += NT) cnt[b] = 0;
-      __syncthreads();
       cur = s;
     }
     const int nb = T.info.nb;
-    const int64_t row = T.info.soff + (t - T.info.tile0) * nb;
-    for (int b = threadIdx.x; b < nb; b += NT) P.status[row + b] = 0ull;
-    const int64_t base = T.start + (t - T.info.tile0) * S::TILE;
-    const int64_t rem = T.start + T.size - base;
-    const int tn = rem < S::TILE ? (int)rem : S::TILE;
-#pragma unroll 4
-    for (int j = 0; j < S::ITEMS; ++j) {
-      const int i = w * 32 * S::ITEMS + j * 32 + lane;
-      unsigned b = (unsigned)nb;
-      if (i < tn) b = bucket_of<K>(T, ld_key<K>(src + base + i));
-      const unsigned peers = __match_any_sync(0xffffffffu, b);
-      if (lane == __ffs(peers) - 1) atomicAdd(&cnt[b], (unsigned)__popc(peers));
+    const int64_t lr = r - T.info.blk0;
+    if (lr % S::CH == 0) {  // this chunk's look-back status starts empty
+      const int64_t row = T.info.soff + (lr / S::CH) * nb;
+      for (int b = threadIdx.x; b < nb; b += NT) P.status[row + b] = 0ull;
     }
+    for (int b = threadIdx.x; b < NB_PAD; b += NT) cnt[b] = 0;
+    __syncthreads();
+    const int64_t b0 = T.start + lr * S::BLK;
+    const int64_t brem = T.start + T.size - b0;
+    for (int sub = 0; sub < S::BLK_TILES; ++sub) {
+      const int64_t tb = (int64_t)sub * S::TILE;
+      if (tb >= brem) break;
+      const int tn = brem - tb < S::TILE ? (int)(brem - tb) : S::TILE;
+      const K *ts = src + b0 + tb;
+      K key[S::ITEMS];
+#pragma unroll
+      for (int j = 0; j < S::ITEMS; ++j) {
+        const int i = w * 32 * S::ITEMS + j * 32 + lane;
+        key[j] = i < tn ? ld_key<K>(ts + i) : (K)0;
+      }
+#pragma unroll
+      for (int j = 0; j < S::ITEMS; ++j) {
+        const int i = w * 32 * S::ITEMS + j * 32 + lane;
+        if (i < tn) atomicAdd(&cnt[bucket_of<K>(T, key[j])], 1u);
+      }
+    }
+    __syncthreads();
+    unsigned *row = P.cmat + T.info.coff + lr * nb;
+    for (int b = threadIdx.x; b < nb; b += NT) row[b] = cnt[b];
+    __syncthreads();
   }
-  if (cur >= 0) flush();
+}
+
+// ------------------------------------------------- count-matrix scan
+// Exclusive scan of every column of a subproblem's count matrix (offset of
+// each bucket's records of block r among that bucket's records) as one pass
+// over chunks of CH rows with decoupled look-back across chunks.  The last
+// chunk of a subproblem also yields the bucket totals.
+template <typename K, bool HV>
+__device__ void phase_mscan(const Params &P, int level, unsigned char *smem) {
+  using S = Shape<K, HV>;
+  Ctl *c = P.ctl;
+  const int64_t nseg = min(ld_cg64(&c->nseg[level & 1]), (long long)P.maxseg);
+  const int64_t nchunks = ld_cg64(&c->nchunks);
+  long long *chunk_sh = (long long *)smem;
+  SegInfo *Is = (SegInfo *)(smem + 16);
+  while (true) {
+    if (threadIdx.x == 0) *chunk_sh = atomic_add_ll(&c->chunk_ctr, 1ll);
+    __syncthreads();
+    const int64_t ch = *chunk_sh;
+    if (ch >= nchunks) break;
+    if (threadIdx.x == 0) *Is = ldcg_obj(&P.info[find_chk_seg(P, nseg, ch)]);
+    __syncthreads();
+    const SegInfo I = *Is;
+    const int nb = I.nb;
+    const int64_t lc = ch - I.chk0;
+    const int64_t rb = lc * S::CH;
+    const int64_t re = rb + S::CH < I.nblk ? rb + S::CH : I.nblk;
+    const bool mute = P.debug_fault == 1 && level == 0 && ch == 1;
+    unsigned *C = P.cmat + I.coff;
+    unsigned long long *st = P.status + I.soff;
+    for (int b = threadIdx.x; b < nb; b += NT) {
+      unsigned long long sum = 0;
+      for (int64_t r = rb; r < re; ++r) sum += __ldcg(C + r * nb + b);
+      unsigned long long excl = 0;
+      if (lc == 0) {
+        st_relaxed(&st[b], (2ull << 62) | sum);
+      } else {
+        if (!mute) st_relaxed(&st[lc * nb + b], (1ull << 62) | sum);
+        int64_t q = lc - 1;
+        const unsigned long long t0 = gtimer();
+        unsigned ns = 32;
+        bool timed_out = false;
+        while (true) {
+          const unsigned long long v = ld_relaxed(&st[q * nb + b]);
+          const unsigned f = (unsigned)(v >> 62);
+          if (f == 0) {
+            if (gtimer() - t0 > P.wait_ns) {
+              timed_out = true;
+              break;
+            }
+            __nanosleep(ns);
+            ns = ns < 512 ? ns * 2 : 512;
+            continue;
+          }
+          excl += v & ((1ull << 62) - 1);
+          if (f == 2) break;
+          --q;
+        }
+        if (timed_out) {
+          latch(P, ERR_TIMEOUT);
+          __threadfence();
+        }
+        if (!mute) st_relaxed(&st[lc * nb + b], (2ull << 62) | (excl + sum));
+      }
+      unsigned long long run = excl;
+      for (int64_t r = rb; r < re; ++r) {
+        const unsigned v = __ldcg(C + r * nb + b);
+        C[r * nb + b] = (unsigned)run;
+        run += v;
+      }
+      if (re == I.nblk) P.bcount[I.boff + b] = (long long)run;
+    }
+    __syncthreads();
+  }
 }
 
 // ------------------------------------------------------------------- scan
@@ -487,12 +581,16 @@ __device__ void phase_scan(const Params &P, int level, unsigned char *smem) {
 }
 
 // ---------------------------------------------------------------- scatter
+// Stable counting-sort scatter: block r writes bucket b's records starting at
+// bstart[b] + X[r][b]; inside the block, tiles of TILE records are ranked by
+// warp match in input order and staged in shared memory in bucket order so
+// that each bucket's run is written contiguously.
 template <typename K, bool HV>
 __device__ void phase_scatter(const Params &P, int level, unsigned char *smem) {
   using S = Shape<K, HV>;
   Ctl *c = P.ctl;
   const int64_t nseg = min(ld_cg64(&c->nseg[level & 1]), (long long)P.maxseg);
-  const int64_t ntiles = ld_cg64(&c->ntiles);
+  const int64_t nblocks = ld_cg64(&c->nblocks);
   const int srcb = level & 1, dstb = srcb ^ 1;
   const K *src = (const K *)P.keys[srcb];
   K *dst = (K *)P.keys[dstb];
@@ -509,152 +607,121 @@ __device__ void phase_scatter(const Params &P, int level, unsigned char *smem) {
   unsigned *tcnt = cv.take<unsigned>(NB_PAD);
   unsigned *toff = cv.take<unsigned>(NB_PAD);
   long long *gbase = cv.take<long long>(NB_PAD);
+  long long *base = cv.take<long long>(NB_PAD);
   unsigned *sh = cv.take<unsigned>(NWARP + 1);
-  long long *tile_sh = cv.take<long long>(1);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   uint16_t *mywc = wcnt + w * NB_PAD;
+  const int64_t r0 = nblocks * blockIdx.x / gridDim.x;
+  const int64_t r1 = nblocks * (blockIdx.x + 1) / gridDim.x;
   int cur = -1;
-  while (true) {
-    if (threadIdx.x == 0) *tile_sh = atomic_add_ll(&c->tile_ctr, 1ll);
-    __syncthreads();
-    const int64_t t = *tile_sh;
-    if (t >= ntiles) break;
+  for (int64_t r = r0; r < r1; ++r) {
     int s = cur;
-    if (cur < 0 || t < T.info.tile0 || t >= T.info.tile0 + T.info.ntiles)
-      s = find_tile_seg(P, nseg, t);
+    if (cur < 0 || r >= T.info.blk0 + T.info.nblk) s = find_blk_seg(P, nseg, r);
     if (s != cur) {
       load_tables<K>(P, s, level, T, lid_s, hk_s, hid_s);
       cur = s;
     }
     const int nb = T.info.nb;
-    const int64_t lt = t - T.info.tile0;
-    const int64_t base = T.start + lt * S::TILE;
-    const int64_t rem = T.start + T.size - base;
-    const int tn = rem < S::TILE ? (int)rem : S::TILE;
-    for (int i = threadIdx.x; i < NWARP * NB_PAD; i += NT) wcnt[i] = 0;
-    __syncthreads();
-    // keys in, bucket ids, warp ranks (item order = input order)
-    K key[S::ITEMS];
-    unsigned br[S::ITEMS];  // bucket << 16 | rank within warp
-#pragma unroll
-    for (int j = 0; j < S::ITEMS; ++j) {
-      const int i = w * 32 * S::ITEMS + j * 32 + lane;
-      key[j] = i < tn ? ld_key<K>(src + base + i) : (K)0;
-    }
-#pragma unroll
-    for (int j = 0; j < S::ITEMS; ++j) {
-      const int i = w * 32 * S::ITEMS + j * 32 + lane;
-      unsigned b = (unsigned)nb;
-      if (i < tn) b = bucket_of<K>(T, key[j]);
-      const unsigned r = warp_rank(b, mywc);
-      br[j] = (b << 16) | r;
-    }
-    __syncthreads();
-    // per bucket: exclusive prefix over warps, tile total
-    for (int b = threadIdx.x; b < nb; b += NT) {
-      unsigned run = 0;
-#pragma unroll
-      for (int q = 0; q < NWARP; ++q) {
-        const unsigned x = wcnt[q * NB_PAD + b];
-        wcnt[q * NB_PAD + b] = (uint16_t)run;
-        run += x;
-      }
-      tcnt[b] = run;
-    }
-    __syncthreads();
-    {
-      const int b0 = 2 * threadIdx.x, b1 = b0 + 1;
-      const unsigned v0 = b0 < nb ? tcnt[b0] : 0u, v1 = b1 < nb ? tcnt[b1] : 0u;
-      unsigned tot;
-      const unsigned o = block_excl_scan<unsigned>(v0 + v1, sh, tot);
-      if (b0 < NB_PAD) toff[b0] = o;
-      if (b1 < NB_PAD) toff[b1] = o + v0;
-    }
-    __syncthreads();
-    // decoupled look-back across the segment's tiles, one thread per bucket
-    const int64_t srow = T.info.soff + lt * nb;
-    const bool mute = P.debug_fault == 1 && level == 0 && t == 1;
-    for (int b = threadIdx.x; b < nb; b += NT) {
-      const unsigned long long agg = tcnt[b];
-      long long excl;
-      if (lt == 0) {
-        excl = __ldcg((const long long *)&P.bstart[T.info.boff + b]);
-        st_relaxed(&P.status[srow + b], (2ull << 62) | (unsigned long long)(excl + (long long)agg));
-      } else {
-        if (!mute) st_relaxed(&P.status[srow + b], (1ull << 62) | agg);
-        long long acc = 0;
-        int64_t q = lt - 1;
-        const unsigned long long tstart = gtimer();
-        bool timed_out = false;
-        while (true) {
-          const unsigned long long v = ld_relaxed(&P.status[T.info.soff + q * nb + b]);
-          const unsigned f = (unsigned)(v >> 62);
-          if (f == 0) {
-            if (gtimer() - tstart > P.wait_ns) {
-              timed_out = true;
-              break;
-            }
-            continue;
-          }
-          acc += (long long)(v & ((1ull << 62) - 1));
-          if (f == 2) break;
-          --q;
-        }
-        excl = acc;
-        if (timed_out) {
-          // latch first, then publish, so a successor that reads this status
-          // also sees the error and writes nothing
-          latch(P, ERR_TIMEOUT);
-          __threadfence();
-        }
-        if (!mute)
-          st_relaxed(&P.status[srow + b], (2ull << 62) | (unsigned long long)(excl + (long long)agg));
-      }
-      gbase[b] = excl - (long long)toff[b];
-    }
-    __syncthreads();
-    // after an error nothing more is written; every destination is also
-    // checked against the subproblem's range
-    __threadfence();
-    const bool stop = *(volatile int *)&c->error != 0;
+    const int64_t lr = r - T.info.blk0;
+    const unsigned *X = P.cmat + T.info.coff + lr * nb;
+    for (int b = threadIdx.x; b < nb; b += NT)
+      base[b] = __ldcg((const long long *)&P.bstart[T.info.boff + b]) + (long long)__ldcg(X + b);
+    const int64_t b0 = T.start + lr * S::BLK;
+    const int64_t brem = T.start + T.size - b0;
     const int64_t lo_ok = T.start, hi_ok = T.start + T.size;
-    // stage keys in bucket order, then write each bucket's run contiguously
-    unsigned pos[S::ITEMS];
+    for (int sub = 0; sub < S::BLK_TILES; ++sub) {
+      const int64_t tb = (int64_t)sub * S::TILE;
+      if (tb >= brem) break;
+      const int tn = brem - tb < S::TILE ? (int)(brem - tb) : S::TILE;
+      const int64_t tbase = b0 + tb;
+      for (int i = threadIdx.x; i < NWARP * NB_PAD; i += NT) wcnt[i] = 0;
+      __syncthreads();
+      // keys in, bucket ids, warp ranks (item order = input order)
+      K key[S::ITEMS];
+      unsigned br[S::ITEMS];  // bucket << 16 | rank within warp
 #pragma unroll
-    for (int j = 0; j < S::ITEMS; ++j) {
-      const int i = w * 32 * S::ITEMS + j * 32 + lane;
-      pos[j] = 0xFFFFFFFFu;
-      if (i < tn) {
-        const unsigned b = br[j] >> 16;
-        pos[j] = toff[b] + wcnt[w * NB_PAD + b] + (br[j] & 0xFFFFu);
-        stage[pos[j]] = key[j];
-        bid[pos[j]] = (uint16_t)b;
+      for (int j = 0; j < S::ITEMS; ++j) {
+        const int i = w * 32 * S::ITEMS + j * 32 + lane;
+        key[j] = i < tn ? ld_key<K>(src + tbase + i) : (K)0;
       }
-    }
-    __syncthreads();
-    if (!stop) {
+      const int nbits = 32 - __clz(nb);  // bits of ids 0..nb (nb = dummy)
+#pragma unroll
+      for (int j = 0; j < S::ITEMS; ++j) {
+        const int i = w * 32 * S::ITEMS + j * 32 + lane;
+        unsigned b = (unsigned)nb;
+        if (i < tn) b = bucket_of<K>(T, key[j]);
+        const unsigned rk = warp_rank_peers(b, warp_peers(b, nbits), mywc);
+        br[j] = (b << 16) | rk;
+      }
+      __syncthreads();
+      // per bucket: exclusive prefix over warps, tile total
+      for (int b = threadIdx.x; b < nb; b += NT) {
+        unsigned run = 0;
+#pragma unroll
+        for (int q = 0; q < NWARP; ++q) {
+          const unsigned x = wcnt[q * NB_PAD + b];
+          wcnt[q * NB_PAD + b] = (uint16_t)run;
+          run += x;
+        }
+        tcnt[b] = run;
+      }
+      __syncthreads();
+      {
+        const int i0 = 2 * threadIdx.x, i1 = i0 + 1;
+        const unsigned v0 = i0 < nb ? tcnt[i0] : 0u, v1 = i1 < nb ? tcnt[i1] : 0u;
+        unsigned tot;
+        const unsigned o = block_excl_scan<unsigned>(v0 + v1, sh, tot);
+        if (i0 < NB_PAD) toff[i0] = o;
+        if (i1 < NB_PAD) toff[i1] = o + v0;
+      }
+      __syncthreads();
+      for (int b = threadIdx.x; b < nb; b += NT) {
+        gbase[b] = base[b] - (long long)toff[b];
+        base[b] += tcnt[b];
+      }
+      // stage keys in bucket order, then write each bucket's run contiguously;
+      // br[j] becomes the item's slot in the staged tile
+#pragma unroll
+      for (int j = 0; j < S::ITEMS; ++j) {
+        const int i = w * 32 * S::ITEMS + j * 32 + lane;
+        if (i < tn) {
+          const unsigned b = br[j] >> 16;
+          const unsigned pj = toff[b] + wcnt[w * NB_PAD + b] + (br[j] & 0xFFFFu);
+          stage[pj] = key[j];
+          bid[pj] = (uint16_t)b;
+          br[j] = pj;
+        }
+      }
+      // value loads go out before the key stores so that both overlap
+      K val[HV ? S::ITEMS : 1];
+      if constexpr (HV) {
+#pragma unroll
+        for (int j = 0; j < S::ITEMS; ++j) {
+          const int i = w * 32 * S::ITEMS + j * 32 + lane;
+          val[j] = i < tn ? ld_key<K>(vsrc + tbase + i) : (K)0;
+        }
+      }
+      __syncthreads();
       for (int q = threadIdx.x; q < tn; q += NT) {
         const int64_t d = gbase[bid[q]] + q;
         if (d >= lo_ok && d < hi_ok) dst[d] = stage[q];
         else latch(P, ERR_INTERNAL);
       }
-    }
-    if constexpr (HV) {
-      __syncthreads();
+      if constexpr (HV) {
+        __syncthreads();
 #pragma unroll
-      for (int j = 0; j < S::ITEMS; ++j) {
-        const int i = w * 32 * S::ITEMS + j * 32 + lane;
-        if (i < tn) stage[pos[j]] = ld_key<K>(vsrc + base + i);
-      }
-      __syncthreads();
-      if (!stop) {
+        for (int j = 0; j < S::ITEMS; ++j) {
+          const int i = w * 32 * S::ITEMS + j * 32 + lane;
+          if (i < tn) stage[br[j]] = val[j];
+        }
+        __syncthreads();
         for (int q = threadIdx.x; q < tn; q += NT) {
           const int64_t d = gbase[bid[q]] + q;
           if (d >= lo_ok && d < hi_ok) vdst[d] = stage[q];
         }
       }
+      __syncthreads();
     }
-    __syncthreads();
   }
 }
 
@@ -698,9 +765,30 @@ __device__ void phase_finish(const Params &P, int level, unsigned char *smem) {
       continue;
     }
     const int n = (int)tk.size;
-    for (int i = threadIdx.x; i < n; i += NT) {
-      ka[i] = ld_key<K>(ksrc + tk.start + i);
-      if constexpr (HV) va[i] = ld_key<K>(vsrc + tk.start + i);
+    {
+      K kr[S::FIN_IT];
+#pragma unroll
+      for (int j = 0; j < S::FIN_IT; ++j) {
+        const int i = j * NT + threadIdx.x;
+        if (i < n) kr[j] = ld_key<K>(ksrc + tk.start + i);
+      }
+#pragma unroll
+      for (int j = 0; j < S::FIN_IT; ++j) {
+        const int i = j * NT + threadIdx.x;
+        if (i < n) ka[i] = kr[j];
+      }
+      if constexpr (HV) {
+#pragma unroll
+        for (int j = 0; j < S::FIN_IT; ++j) {
+          const int i = j * NT + threadIdx.x;
+          if (i < n) kr[j] = ld_key<K>(vsrc + tk.start + i);
+        }
+#pragma unroll
+        for (int j = 0; j < S::FIN_IT; ++j) {
+          const int i = j * NT + threadIdx.x;
+          if (i < n) va[i] = kr[j];
+        }
+      }
     }
     __syncthreads();
     K *kin = ka, *kout = kb, *vin = va, *vout = vb;
@@ -719,7 +807,7 @@ __device__ void phase_finish(const Params &P, int level, unsigned char *smem) {
         if (w * 32 * S::FIN_IT + j * 32 < n) {  // warp-uniform
           unsigned d = 1u << FIN_DIG;  // dummy digit
           if (i < n) d = (unsigned)((uint64_t)kin[i] >> shift) & dmask;
-          const unsigned r = warp_rank(d, mywc);
+          const unsigned r = warp_rank_peers(d, warp_peers_fixed<FIN_DIG + 1>(d), mywc);
           dr[j] = (d << 16) | r;
         }
       }
@@ -918,6 +1006,10 @@ __global__ void __launch_bounds__(NT, 2) dtsort_kernel(const Params P) {
       phase_hist<K, HV>(P, level, smem);
       grid_sync(P);
       tick(P, PH_HIST);
+      phase_mscan<K, HV>(P, level, smem);
+      grid_sync(P);
+      tick(P, PH_SCAN);
+      if (*(volatile int *)&c->err_snap) break;  // offsets unusable
       phase_scan<K, HV>(P, level, smem);
       grid_sync(P);
       tick(P, PH_SCAN);

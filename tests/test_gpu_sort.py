@@ -271,9 +271,10 @@ def test_argument_checks(G):
 
 
 def test_bounded_wait_expires_without_hanging(G):
-    # a tile that never publishes its look-back status: the successors' waits
-    # run out, the sort latches DEVICE_TIMEOUT and the context stays usable
-    n = 200_000
+    # a look-back chunk that never publishes its status: the successors'
+    # waits run out, the sort latches DEVICE_TIMEOUT and the context stays
+    # usable (3M records = several chunks of the level-0 count matrix)
+    n = 3_000_000
     keys = gen.family("uniform", n, np.uint32, seed=4)
     vals = gen.iota(n, np.uint32)
     G.set_options(debug_fault=1, wait_limit_ms=50)
