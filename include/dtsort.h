@@ -198,6 +198,32 @@ DTSORT_API dtsort_status dtsort_last_device_error(dtsort_handle h, dtsort_stream
 /* Copies the statistics of the most recent sort (synchronises the device). */
 DTSORT_API dtsort_status dtsort_get_stats(dtsort_handle h, dtsort_stats *out);
 
+/* ---- sorting without any allocation ---------------------------------------
+ * The paper has no counterpart of this entry point.  It serves callers that
+ * may not allocate device memory at call time and cannot provide a workspace
+ * either: code running while a CUDA stream is captured, plugin or callback
+ * code that gets a stream from a host framework owning all device memory,
+ * real-time pipelines that forbid allocation after start-up.
+ *
+ * Same operation as dtsort_u32_kv (stable sort of keys[0..n) with values
+ * alongside, in place, default options), but every temporary lives in one
+ * static device array of 12 MiB inside this library, which each GPU that
+ * loads the library holds until the process exits; no cudaMalloc/cudaFree
+ * and no allocating library routine is called.  n must not exceed
+ * DTSORT_NOALLOC_MAX_N (larger n returns DTSORT_ERR_INVALID_ARG without
+ * launching).  keys/values: device pointers on the current device, 4-byte
+ * aligned.  device_status: optional device int32 the sort latches its device
+ * status into (0 = OK; cleared at the start of the call); NULL to ignore.
+ * The first call on a device performs a one-time set-up on that device
+ * (looks up the array's device address, sets the kernel's shared-memory
+ * limit); make that first call before any stream capture.  All calls share
+ * the one array (it keeps the last call's contents; the call clears what must
+ * start at zero), so calls that overlap on the GPU race with each other:
+ * order them on one stream. */
+#define DTSORT_NOALLOC_MAX_N ((int64_t)1 << 20)
+DTSORT_API dtsort_status dtsort_u32_kv_noalloc(uint32_t *keys, uint32_t *values, int64_t n,
+                                               int32_t *device_status, dtsort_stream stream);
+
 /* ---- diagnostics: single steps of the method, for testing ---------------- */
 
 /* Alg. 2 step 1 on one subproblem keys[start .. start+size) of an array whose

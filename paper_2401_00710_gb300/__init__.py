@@ -34,7 +34,11 @@ EXPORTED = [
     "dtsort_u64_kv", "dtsort_segmented_u32", "dtsort_segmented_u32_kv",
     "dtsort_segmented_u64", "dtsort_segmented_u64_kv",
     "dtsort_last_device_error", "dtsort_get_stats", "dtsort_debug_sample",
+    "dtsort_u32_kv_noalloc",
 ]
+
+# largest n of dtsort_u32_kv_noalloc (DTSORT_NOALLOC_MAX_N in dtsort.h)
+DTSORT_NOALLOC_MAX_N = 1 << 20
 
 
 class DtsortError(RuntimeError):
@@ -144,6 +148,7 @@ def _declare(L):
     L.dtsort_debug_sample.argtypes = [_H, _P, ctypes.c_int, _I64, _I64,
                                       ctypes.c_int, ctypes.c_uint64, _I64, _I64,
                                       _P, _P, _P, _P]
+    L.dtsort_u32_kv_noalloc.argtypes = [_P, _P, _I64, _P, _P]
     for name in EXPORTED:
         if name != "dtsort_status_string":
             getattr(L, name).restype = _ST
@@ -251,6 +256,11 @@ def dtsort_debug_sample(h, keys, key_bytes, start, size, hi, seed, count, L,
     return lib().dtsort_debug_sample(h, keys, key_bytes, start, size, hi, seed,
                                      count, L, heavy_out, nheavy_out, max_out,
                                      stream or None)
+
+
+def dtsort_u32_kv_noalloc(keys, values, n, device_status=None, stream=0):
+    """The allocation-free 32-bit key/value sort (n <= DTSORT_NOALLOC_MAX_N)."""
+    return lib().dtsort_u32_kv_noalloc(keys, values, n, device_status, stream or None)
 
 
 # ---- PyTorch convenience ----------------------------------------------------
