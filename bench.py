@@ -46,6 +46,18 @@ def parse():
     ap.add_argument("--cpu-sample", type=int, default=100_000_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--launch-mode", type=int, default=0,
+                    help="1: one launch per phase (profiling aid)")
+    ap.add_argument("--workload", default="single", choices=["single", "segmented"])
+    ap.add_argument("--seg-total", default="2e8",
+                    help="segmented: total records ('literal' = sizes as drawn)")
+    ap.add_argument("--segments", type=int, default=4096)
+    ap.add_argument("--graph", action="store_true",
+                    help="segmented: capture the call once, replay it per step")
+    ap.add_argument("--baseline-calls", action="store_true",
+                    help="segmented: also time one dtsort_u32_kv call per array")
+    ap.add_argument("--autotune", action="store_true",
+                    help="run the autotuner on the workload first and use its choice")
     return ap.parse_args()
 
 
@@ -209,6 +221,10 @@ def run_ours(args):
     op = {"u32kv": dts.DTSORT_OP_U32_KV, "u32": dts.DTSORT_OP_U32,
           "u64kv": dts.DTSORT_OP_U64_KV, "u64": dts.DTSORT_OP_U64}[args.op]
     h = dts.dtsort_create(local)
+    if args.launch_mode:
+        o = dts.dtsort_get_options(h)
+        o.launch_mode = args.launch_mode
+        dts.dtsort_set_options(h, o)
     wsb = dts.dtsort_workspace_bytes(h, op, n)
     ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
@@ -328,10 +344,157 @@ def run_ours(args):
     return 0
 
 
+def segmented_passes(size, cap, gamma=9):
+    """Distribution passes + base case the method needs for one array."""
+    import math
+    if size <= cap:
+        return 1
+    return 1 + max(1, math.ceil(math.log2(size / (0.7 * cap)) / gamma))
+
+
+def run_segmented(args):
+    """4096 arrays with log-uniform sizes in [100, 10^7], u32 keys (uniform or
+    Zipf 1.0 per array) with int32 values, sorted by one persistent launch."""
+    import torch
+
+    import gen
+    import paper_2401_00710_gb300 as dts
+
+    rank, world, local = dist_env()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    total = None if args.seg_total == "literal" else float(args.seg_total)
+    off, fam = gen.segmented_layout(nseg=args.segments, lo=100, hi=1e7, seed=args.seed,
+                                    total=total)
+    n = int(off[-1])
+    nseg = len(off) - 1
+    hk = torch.empty(n, dtype=torch.int32, pin_memory=True)
+    hv = torch.empty(n, dtype=torch.int32, pin_memory=True)
+    gen.fill_segmented_u32(hk.data_ptr(), hv.data_ptr(), off, fam, seed=args.seed + rank)
+    pk, pv = hk.to(dev), hv.to(dev)
+    k, v = torch.empty_like(pk), torch.empty_like(pv)
+    o = torch.from_numpy(off).to(dev)
+    h = dts.dtsort_create(local)
+    op = dts.DTSORT_OP_U32_KV
+    stream = torch.cuda.current_stream(dev)
+    sp = stream.cuda_stream
+    tuned = None
+    if args.autotune:
+        o_ = dts.dtsort_get_options(h)
+        o_.autotune = 1
+        dts.dtsort_set_options(h, o_)
+        sb = dts.dtsort_autotune_scratch_bytes(h, op, n, nseg)
+        scratch = torch.empty(sb, dtype=torch.uint8, device=dev)
+        st, best = dts.dtsort_autotune(h, op, pk.data_ptr(), pv.data_ptr(), o.data_ptr(),
+                                       nseg, n, scratch.data_ptr(), sb, sp)
+        if st != 0:
+            raise RuntimeError(dts.status_string(st))
+        tuned = {"gamma_max": best.gamma_max, "finisher_capacity": best.finisher_capacity,
+                 "block_tiles": best.block_tiles}
+        del scratch
+    wsb = dts.dtsort_workspace_bytes(h, op, n, nseg)
+    ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
+
+    def call():
+        st = dts.dtsort_segmented_u32_kv(h, k.data_ptr(), v.data_ptr(), o.data_ptr(), nseg,
+                                         n, ws.data_ptr(), wsb, sp)
+        if st != 0:
+            raise RuntimeError(dts.status_string(st))
+
+    graph = None
+    if args.graph:
+        k.copy_(pk)
+        v.copy_(pv)
+        torch.cuda.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            sp = torch.cuda.current_stream(dev).cuda_stream
+            call()
+        sp = stream.cuda_stream
+
+    def step():
+        if graph is not None:
+            graph.replay()
+        else:
+            call()
+
+    def timed(fn, steps, warmup):
+        for _ in range(warmup):
+            k.copy_(pk)
+            v.copy_(pv)
+            fn()
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(steps):
+            k.copy_(pk)
+            v.copy_(pv)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        return sum(ms) / len(ms), ms
+
+    with ClockSampler(local) as clk:
+        ms_step, ms_list = timed(step, args.steps, args.warmup)
+    st = dts.dtsort_last_device_error(h, sp)
+    if st != 0:
+        raise RuntimeError("device: " + dts.status_string(st))
+    stats = dts.dtsort_get_stats(h).as_dict()
+    base = None
+    if args.baseline_calls:
+        sizes = np.diff(off)
+
+        def separate():
+            for s_ in range(nseg):
+                a_, b_ = int(off[s_]), int(off[s_ + 1])
+                if b_ - a_ < 2:
+                    continue
+                st_ = dts.dtsort_u32_kv(h, k.data_ptr() + 4 * a_, v.data_ptr() + 4 * a_, b_ - a_,
+                                        ws.data_ptr(), wsb, sp)
+                if st_ != 0:
+                    raise RuntimeError(dts.status_string(st_))
+        b_ms, _ = timed(separate, max(1, min(args.steps, 2)), 1)
+        base = {"ms_per_step": b_ms, "value": n / (b_ms / 1e3), "unit": "keys/s",
+                "what": "one dtsort_u32_kv call per array, same GPU, same stream"}
+        del sizes
+    cap = 6144
+    b_alg = sum(int(sz) * (4 + segmented_passes(int(sz), cap) * 2 * 8) for sz in np.diff(off))
+    peak, peak_kind = peaks()
+    achieved = b_alg / (ms_step / 1e3) / 1e9
+    line = {
+        "metric": METRIC, "value": n / (ms_step / 1e3), "unit": "keys/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32kv",
+        "data": "synthetic",
+        "config": {"workload": "batched segmented sort: %d arrays, sizes log-uniform in "
+                               "[100, 1e7]%s, u32 keys uniform or Zipf 1.0 per array, int32 "
+                               "values" % (nseg, "" if total is None else
+                                           " scaled to %.3g records" % total),
+                   "n": n, "segments": nseg, "graph": bool(args.graph),
+                   "autotuned": tuned},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+                     "bytes": b_alg},
+        "gpu_launches": args.steps, "clocks": clk.summary(),
+        "baseline_separate_calls": base,
+        "stats": {"levels": stats["levels"], "phase_ms": stats["phase_ms"],
+                  "finisher_tasks": stats["finisher_tasks"]},
+        "ms_steps": ms_list,
+    }
+    print(json.dumps(line), flush=True)
+    dts.dtsort_destroy(h)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "segmented":
+        return run_segmented(args)
     return run_ours(args)
 
 

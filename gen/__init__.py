@@ -132,3 +132,34 @@ def fill_family(name, out_ptr, n, dtype=np.uint32, seed=1, nthreads=0):
         p1 = 10.0 / max(n, 1)
     fill_keys(out_ptr, n, kind, np.dtype(dt).itemsize, seed, p1, p2,
               nthreads=nthreads)
+
+
+# ---- the batched segmented configuration ------------------------------------
+def segmented_layout(nseg=4096, lo=100.0, hi=1e7, seed=1, total=None):
+    """Sizes log-uniform in [lo, hi] (seeded), one family flag per array
+    (0 uniform, 1 Zipf s=1.0 over 10^9) with probability 1/2.  With `total`,
+    sizes are scaled so that they sum to about `total` (each at least lo).
+    Returns (offsets int64[nseg+1], family int32[nseg])."""
+    sizes, fam = segment_sizes(nseg, lo, hi, seed)
+    if total is not None:
+        sizes = np.maximum(np.floor(sizes * (float(total) / sizes.sum())), lo).astype(np.int64)
+    off = np.zeros(nseg + 1, dtype=np.int64)
+    np.cumsum(sizes, out=off[1:])
+    return off, fam
+
+
+def fill_segmented_u32(keys_ptr, vals_ptr, offsets, family, seed=1, nthreads=0):
+    """Keys of array s: uniform u32 or Zipf(1.0) ranks - 1, from the stream
+    seeded with seed*65536 + s; values: index within the array."""
+    for s in range(len(offsets) - 1):
+        a, b = int(offsets[s]), int(offsets[s + 1])
+        if b <= a:
+            continue
+        if family[s]:
+            kind, p1, p2 = ZIPF, 1.0, 1e9
+        else:
+            kind, p1, p2 = UNIFORM, 0.0, 0.0
+        fill_keys(keys_ptr + 4 * a, b - a, kind, 4, seed * 65536 + s, p1, p2,
+                  nthreads=nthreads if b - a > (1 << 16) else 1)
+        if vals_ptr is not None:
+            lib().gen_iota(4, 0, b - a, vals_ptr + 4 * a)

@@ -28,7 +28,8 @@
  *     the host can check before launching.  Errors found on the device (a
  *     bounded wait that timed out, an exhausted internal table) are latched
  *     in the handle and read with dtsort_last_device_error().
- *   - No call allocates device memory, except dtsort_create() (a few KB).
+ *   - No call allocates device memory, except dtsort_create() (a few KB) and
+ *     the first sort with launch_mode 1 (a pinned host copy of a few KB).
  *   - n == 0 is a no-op returning DTSORT_OK; n >= 2^32 returns
  *     DTSORT_ERR_UNSUPPORTED.  n < 0, or a NULL pointer where
  *     n > 0 needs one, returns DTSORT_ERR_INVALID_ARG.  A workspace smaller
@@ -101,7 +102,15 @@ typedef struct {
   int32_t debug_fault;       /* testing only: 1 = the second look-back chunk of
                                 the first distribution never publishes its
                                 status, so its successors' waits expire */
-  int32_t reserved[6];
+  int32_t launch_mode;       /* 0: one persistent cooperative launch per sort
+                                (default, no host synchronisation);
+                                1: one launch per phase with the level loop on
+                                the host (a profiling aid: every phase appears
+                                as its own kernel; synchronises the stream) */
+  int32_t block_tiles;       /* rows of the per-level count matrix cover
+                                block_tiles tiles of the scatter (8K 32-bit or
+                                4K 64-bit keys each); 1..8, default 4 */
+  int32_t reserved[4];
 } dtsort_options;
 
 /* Statistics of the last completed sort on this handle (read after sync). */
@@ -197,6 +206,26 @@ DTSORT_API dtsort_status dtsort_last_device_error(dtsort_handle h, dtsort_stream
 
 /* Copies the statistics of the most recent sort (synchronises the device). */
 DTSORT_API dtsort_status dtsort_get_stats(dtsort_handle h, dtsort_stats *out);
+
+/* ---- autotuning ------------------------------------------------------------
+ * Picks the tuning knobs (digit width limit, base-case capacity, count-matrix
+ * block size) for one problem class; the output never depends on them.  Each
+ * candidate setting sorts a private copy of keys/values (+offsets) placed in
+ * `scratch` (DEVICE, at least dtsort_autotune_scratch_bytes(), 256-byte
+ * aligned); the caller's arrays are only read.  The fastest setting is
+ * stored in the handle's options and written to the on-disk cache (the file
+ * named by the environment variable DTSORT_AUTOTUNE_CACHE, else
+ * $HOME/.cache/dtsort_autotune.tsv), keyed by (GPU name, op, floor(log2 n),
+ * floor(log2 num_segments)).  Sorts on a handle whose options have
+ * autotune = 1 use the cached setting of their class when there is one.
+ * Synchronises `stream`.  best_out (optional) receives the chosen options. */
+DTSORT_API dtsort_status dtsort_autotune_scratch_bytes(dtsort_handle h, dtsort_op op, int64_t n,
+                                                       int64_t num_segments, size_t *bytes);
+DTSORT_API dtsort_status dtsort_autotune(dtsort_handle h, dtsort_op op, const void *keys,
+                                         const void *values, const int64_t *offsets,
+                                         int64_t num_segments, int64_t n, void *scratch,
+                                         size_t scratch_bytes, dtsort_stream stream,
+                                         dtsort_options *best_out);
 
 /* ---- sorting without any allocation ---------------------------------------
  * The paper has no counterpart of this entry point.  It serves callers that

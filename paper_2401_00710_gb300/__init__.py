@@ -34,7 +34,7 @@ EXPORTED = [
     "dtsort_u64_kv", "dtsort_segmented_u32", "dtsort_segmented_u32_kv",
     "dtsort_segmented_u64", "dtsort_segmented_u64_kv",
     "dtsort_last_device_error", "dtsort_get_stats", "dtsort_debug_sample",
-    "dtsort_u32_kv_noalloc",
+    "dtsort_u32_kv_noalloc", "dtsort_autotune", "dtsort_autotune_scratch_bytes",
 ]
 
 # largest n of dtsort_u32_kv_noalloc (DTSORT_NOALLOC_MAX_N in dtsort.h)
@@ -60,7 +60,9 @@ class dtsort_options(ctypes.Structure):
                 ("learned_train_steps", ctypes.c_int32),
                 ("wait_limit_ms", ctypes.c_int32),
                 ("debug_fault", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 6)]
+                ("launch_mode", ctypes.c_int32),
+                ("block_tiles", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 4)]
 
 
 class dtsort_stats(ctypes.Structure):
@@ -149,6 +151,10 @@ def _declare(L):
                                       ctypes.c_int, ctypes.c_uint64, _I64, _I64,
                                       _P, _P, _P, _P]
     L.dtsort_u32_kv_noalloc.argtypes = [_P, _P, _I64, _P, _P]
+    L.dtsort_autotune_scratch_bytes.argtypes = [_H, ctypes.c_int, _I64, _I64,
+                                                ctypes.POINTER(_SZ)]
+    L.dtsort_autotune.argtypes = [_H, ctypes.c_int, _P, _P, _P, _I64, _I64, _P, _SZ,
+                                  _P, ctypes.POINTER(dtsort_options)]
     for name in EXPORTED:
         if name != "dtsort_status_string":
             getattr(L, name).restype = _ST
@@ -256,6 +262,24 @@ def dtsort_debug_sample(h, keys, key_bytes, start, size, hi, seed, count, L,
     return lib().dtsort_debug_sample(h, keys, key_bytes, start, size, hi, seed,
                                      count, L, heavy_out, nheavy_out, max_out,
                                      stream or None)
+
+
+def dtsort_autotune_scratch_bytes(h, op, n, num_segments=1):
+    b = _SZ(0)
+    _check(lib().dtsort_autotune_scratch_bytes(h, int(op), int(n), int(num_segments),
+                                               ctypes.byref(b)),
+           "dtsort_autotune_scratch_bytes")
+    return b.value
+
+
+def dtsort_autotune(h, op, keys, values, offsets, num_segments, n, scratch,
+                    scratch_bytes, stream=0):
+    """Returns (status, chosen options)."""
+    best = dtsort_options()
+    st = lib().dtsort_autotune(h, int(op), keys, values, offsets, num_segments, n,
+                               scratch, scratch_bytes, stream or None,
+                               ctypes.byref(best))
+    return st, best
 
 
 def dtsort_u32_kv_noalloc(keys, values, n, device_status=None, stream=0):

@@ -3,9 +3,17 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstdint>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
+#include <string>
+
+#include <sys/stat.h>
 
 #include "../../include/dtsort.h"
 #include "dtsort_launch.h"
@@ -27,7 +35,7 @@ struct Layout {
 };
 
 struct Opts {
-  int gamma_max, cap, heavy_on, sample_factor, debug_fault;
+  int gamma_max, cap, heavy_on, sample_factor, debug_fault, blk_tiles;
   uint64_t seed;
   unsigned long long wait_ns;
 };
@@ -37,6 +45,7 @@ struct Opts {
 struct dtsort_handle_s {
   int device = 0;
   int nsm = 0;
+  void *ctl_host = nullptr;  // pinned copy of the control block (phase launches)
   dtsort_options opt{};
   int *d_status = nullptr;
   DevStats *d_stats = nullptr;
@@ -74,6 +83,7 @@ Opts effective(const dtsort_options &o, const KernelShape &ks) {
   r.sample_factor = o.sample_log_factor > 0 ? o.sample_log_factor : 1;
   r.seed = o.seed ? o.seed : 1;
   r.debug_fault = o.debug_fault;
+  r.blk_tiles = o.block_tiles > 0 ? o.block_tiles : ks.blk / ks.tile;
   r.wait_ns = (unsigned long long)(o.wait_limit_ms > 0 ? o.wait_limit_ms : 2000) * 1000000ull;
   return r;
 }
@@ -81,7 +91,7 @@ Opts effective(const dtsort_options &o, const KernelShape &ks) {
 size_t up(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // Upper bounds of every device table for n records in nsegs arrays.  The
-// digit width rule gives 2^gamma < 2*size/target for every subproblem
+// digit width rule gives 2^gamma < 8*size/target for every subproblem
 // (size > cap > target), which bounds the per-level sums below.
 Layout make_layout(int kb, int vb, int64_t n, int64_t nsegs, const Opts &o,
                    const KernelShape &ks) {
@@ -90,14 +100,17 @@ Layout make_layout(int kb, int vb, int64_t n, int64_t nsegs, const Opts &o,
   L.target = std::max<int64_t>(16, (int64_t)o.cap * 7 / 10);
   const int64_t nt = n / L.target + 1;
   L.maxseg = n / (o.cap + 1) + 2;
-  L.bmax = 3 * nt + L.maxseg + 1024;
-  L.hmax = nt + L.maxseg + 1024;
-  L.zmax = 2 * nt + 2 * L.maxseg + 1024;
-  L.hashmax = 2 * nt + L.maxseg + 1024;
+  // per subproblem 2^gamma < 8 * size / target: buckets <= 1.5 * 2^gamma + 1,
+  // heavy keys <= 2^(gamma-1), light-table entries 2^gamma + 1
+  L.bmax = 12 * nt + L.maxseg + 1024;
+  L.hmax = 4 * nt + L.maxseg + 1024;
+  L.zmax = 8 * nt + 2 * L.maxseg + 1024;
+  L.hashmax = 8 * nt + L.maxseg + 1024;
   // count matrix: one row of <= NB_HW words per block of every subproblem;
   // look-back status: one row per chunk of ks.ch rows
-  L.cwords = (int64_t)dts::NB_HW * (n / ks.blk + 1) + L.bmax;
-  L.swords = (int64_t)dts::NB_HW * (n / ((int64_t)ks.blk * ks.ch) + 1) + L.bmax;
+  const int64_t blk = (int64_t)o.blk_tiles * ks.tile;
+  L.cwords = (int64_t)dts::NB_HW * (n / blk + 1) + L.bmax;
+  L.swords = (int64_t)dts::NB_HW * (n / (blk * ks.ch) + 1) + L.bmax;
   L.tmax = 2 * L.bmax + 2 * (n / dts::COPY_CHUNK + 1) + nsegs + 4096;
   L.mhmax = 4 * L.hmax + 4096;
   size_t off = 0;
@@ -133,6 +146,105 @@ dtsort_status from_cuda(cudaError_t e) {
   return e == cudaSuccess ? DTSORT_OK : DTSORT_ERR_CUDA;
 }
 
+// ---------------------------------------------------------------- autotune
+// Cache of tuned settings, keyed by (GPU name, op, log2 n, log2 arrays).
+struct TuneKey {
+  std::string gpu;
+  int op, ln, ls;
+  bool operator<(const TuneKey &o) const {
+    if (gpu != o.gpu) return gpu < o.gpu;
+    if (op != o.op) return op < o.op;
+    if (ln != o.ln) return ln < o.ln;
+    return ls < o.ls;
+  }
+};
+struct TuneVal {
+  int gamma_max, cap, block_tiles, sample_factor;
+  double ms;
+};
+
+std::mutex g_tune_mu;
+std::map<TuneKey, TuneVal> g_tune;
+bool g_tune_loaded = false;
+
+std::string tune_path() {
+  const char *e = std::getenv("DTSORT_AUTOTUNE_CACHE");
+  if (e && *e) return e;
+  const char *home = std::getenv("HOME");
+  return std::string(home ? home : ".") + "/.cache/dtsort_autotune.tsv";
+}
+
+int log2_class(int64_t x) {
+  int l = 0;
+  while (l < 62 && ((int64_t)1 << (l + 1)) <= x) ++l;
+  return l;
+}
+
+std::string gpu_name(int device) {
+  cudaDeviceProp p;
+  if (cudaGetDeviceProperties(&p, device) != cudaSuccess) return "unknown";
+  std::string s(p.name);
+  for (char &ch : s)
+    if (ch == '\t' || ch == '\n') ch = ' ';
+  return s;
+}
+
+void tune_load_locked() {
+  if (g_tune_loaded) return;
+  g_tune_loaded = true;
+  FILE *f = std::fopen(tune_path().c_str(), "r");
+  if (!f) return;
+  char line[512];
+  while (std::fgets(line, sizeof line, f)) {
+    char gpu[256];
+    int op, ln, ls, g, cap, bt, sf;
+    double ms;
+    if (std::sscanf(line, "%255[^\t]\t%d\t%d\t%d\t%d\t%d\t%d\t%d\t%lf", gpu, &op, &ln, &ls, &g,
+                    &cap, &bt, &sf, &ms) == 9)
+      g_tune[TuneKey{gpu, op, ln, ls}] = TuneVal{g, cap, bt, sf, ms};
+  }
+  std::fclose(f);
+}
+
+void tune_store(const TuneKey &k, const TuneVal &v) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  tune_load_locked();
+  g_tune[k] = v;
+  const std::string path = tune_path();
+  const std::string dir = path.substr(0, path.find_last_of('/'));
+  if (!dir.empty() && dir != path) {
+    std::string cmd = dir;  // create the directory without a shell
+    for (size_t i = 1; i <= cmd.size(); ++i)
+      if (i == cmd.size() || cmd[i] == '/') {
+        const std::string part = cmd.substr(0, i);
+        mkdir(part.c_str(), 0755);
+      }
+  }
+  FILE *f = std::fopen(path.c_str(), "w");
+  if (!f) return;
+  for (const auto &kv : g_tune)
+    std::fprintf(f, "%s\t%d\t%d\t%d\t%d\t%d\t%d\t%d\t%.6f\n", kv.first.gpu.c_str(),
+                 kv.first.op, kv.first.ln, kv.first.ls, kv.second.gamma_max, kv.second.cap,
+                 kv.second.block_tiles, kv.second.sample_factor, kv.second.ms);
+  std::fclose(f);
+}
+
+// The handle's options, with the cached tuned setting applied when
+// options.autotune is set and the cache holds one for this problem class.
+dtsort_options tuned_options(dtsort_handle h, int op, int64_t n, int64_t nsegs) {
+  dtsort_options o = h->opt;
+  if (o.autotune != 1) return o;
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  tune_load_locked();
+  auto it = g_tune.find(TuneKey{gpu_name(h->device), op, log2_class(n), log2_class(nsegs)});
+  if (it == g_tune.end()) return o;
+  o.gamma_max = it->second.gamma_max;
+  o.finisher_capacity = it->second.cap;
+  o.block_tiles = it->second.block_tiles;
+  o.sample_log_factor = it->second.sample_factor;
+  return o;
+}
+
 dtsort_status run_sort(dtsort_handle h, int op, void *keys, void *vals, const int64_t *offsets,
                        int64_t nsegs, int64_t n, void *ws, size_t ws_bytes, cudaStream_t s) {
   if (!h) return DTSORT_ERR_INVALID_ARG;
@@ -151,7 +263,7 @@ dtsort_status run_sort(dtsort_handle h, int op, void *keys, void *vals, const in
   cudaError_t e = get_shape(h, op, &ks);
   if (e != cudaSuccess) return DTSORT_ERR_CUDA;
   if (ks->blocks_per_sm < 1) return DTSORT_ERR_UNSUPPORTED;
-  const Opts o = effective(h->opt, *ks);
+  const Opts o = effective(tuned_options(h, op, n, offsets ? nsegs : 1), *ks);
   const Layout L = make_layout(kb, vb, n, offsets ? nsegs : 1, o, *ks);
   if (ws_bytes < L.total) return DTSORT_ERR_WORKSPACE_TOO_SMALL;
   char *w = (char *)ws;
@@ -171,6 +283,7 @@ dtsort_status run_sort(dtsort_handle h, int op, void *keys, void *vals, const in
   P.seed = o.seed;
   P.sample_factor = o.sample_factor;
   P.debug_fault = o.debug_fault;
+  P.blk_tiles = o.blk_tiles;
   P.wait_ns = o.wait_ns;
   P.ctl = (dts::Ctl *)(w + L.ctl);
   P.segs[0] = (dts::Seg *)(w + L.segs0);
@@ -203,6 +316,17 @@ dtsort_status run_sort(dtsort_handle h, int op, void *keys, void *vals, const in
   e = cudaMemsetAsync(P.ctl, 0, sizeof(dts::Ctl), s);
   if (e != cudaSuccess) return DTSORT_ERR_CUDA;
   const int grid = h->nsm * std::min(ks->blocks_per_sm, 2);
+  if (h->opt.launch_mode == 1) {
+    if (!h->ctl_host && cudaMallocHost(&h->ctl_host, sizeof(dts::Ctl)) != cudaSuccess)
+      return DTSORT_ERR_CUDA;
+    switch (op) {
+      case DTSORT_OP_U32: e = dts::launch_split_u32(P, grid, s, h->ctl_host); break;
+      case DTSORT_OP_U32_KV: e = dts::launch_split_u32kv(P, grid, s, h->ctl_host); break;
+      case DTSORT_OP_U64: e = dts::launch_split_u64(P, grid, s, h->ctl_host); break;
+      default: e = dts::launch_split_u64kv(P, grid, s, h->ctl_host); break;
+    }
+    return from_cuda(e);
+  }
   switch (op) {
     case DTSORT_OP_U32: e = dts::launch_u32(P, grid, s); break;
     case DTSORT_OP_U32_KV: e = dts::launch_u32kv(P, grid, s); break;
@@ -281,6 +405,7 @@ dtsort_status dtsort_create(dtsort_handle *out, int device) {
 
 dtsort_status dtsort_destroy(dtsort_handle h) {
   if (!h) return DTSORT_ERR_INVALID_ARG;
+  if (h->ctl_host) cudaFreeHost(h->ctl_host);
   cudaFree(h->d_status);
   cudaFree(h->d_stats);
   delete h;
@@ -294,7 +419,8 @@ dtsort_status dtsort_set_options(dtsort_handle h, const dtsort_options *opt) {
       opt->sample_log_factor < 0 || opt->sample_log_factor > 64 ||
       (opt->bucketing != DTSORT_BUCKETING_DIGIT && opt->bucketing != DTSORT_BUCKETING_LEARNED) ||
       opt->learned_segments < 0 || opt->learned_train_steps < 0 || opt->wait_limit_ms < 0 ||
-      opt->debug_fault < 0 || opt->debug_fault > 1)
+      opt->debug_fault < 0 || opt->debug_fault > 1 || opt->launch_mode < 0 ||
+      opt->launch_mode > 1 || opt->block_tiles < 0 || opt->block_tiles > 8)
     return DTSORT_ERR_INVALID_ARG;
   h->opt = *opt;
   return DTSORT_OK;
@@ -315,7 +441,7 @@ dtsort_status dtsort_workspace_bytes(dtsort_handle h, dtsort_op op, int64_t n,
   if (cur != h->device && cudaSetDevice(h->device) != cudaSuccess) return DTSORT_ERR_CUDA;
   KernelShape *ks = nullptr;
   if (get_shape(h, op, &ks) != cudaSuccess) return DTSORT_ERR_CUDA;
-  const Opts o = effective(h->opt, *ks);
+  const Opts o = effective(tuned_options(h, op, n, num_segments > 0 ? num_segments : 1), *ks);
   const int kb = key_bytes(op), vb = has_vals(op) ? kb : 0;
   *bytes = make_layout(kb, vb, n, num_segments > 0 ? num_segments : 1, o, *ks).total;
   return DTSORT_OK;
@@ -399,6 +525,113 @@ dtsort_status dtsort_get_stats(dtsort_handle h, dtsort_stats *out) {
   out->learned_bucket_cv = d.learned_cv;
   out->learned_bucket_max_over_mean = d.learned_mom;
   for (int k = 0; k < 8; ++k) out->phase_ms[k] = d.phase_ms[k];
+  return DTSORT_OK;
+}
+
+// Candidate settings tried by the autotuner.
+static const int kTuneGamma[] = {7, 8, 9};
+static const int kTuneCapDiv[] = {4, 3, 2};  // capacity = fin_cap * 2 / div
+static const int kTuneBlk[] = {2, 4};
+
+dtsort_status dtsort_autotune_scratch_bytes(dtsort_handle h, dtsort_op op, int64_t n,
+                                            int64_t num_segments, size_t *bytes) {
+  if (!h || !bytes || n < 0 || num_segments < 0 || (int)op < 0 || (int)op >= kOps)
+    return DTSORT_ERR_INVALID_ARG;
+  int cur = -1;
+  if (cudaGetDevice(&cur) != cudaSuccess) return DTSORT_ERR_CUDA;
+  if (cur != h->device && cudaSetDevice(h->device) != cudaSuccess) return DTSORT_ERR_CUDA;
+  KernelShape *ks = nullptr;
+  if (get_shape(h, op, &ks) != cudaSuccess) return DTSORT_ERR_CUDA;
+  const int kb = key_bytes(op), vb = has_vals(op) ? kb : 0;
+  size_t ws = 0;
+  for (int g : kTuneGamma)
+    for (int cd : kTuneCapDiv)
+      for (int bt : kTuneBlk) {
+        dtsort_options o = h->opt;
+        o.gamma_max = g;
+        o.finisher_capacity = ks->fin_cap * 2 / cd;
+        o.block_tiles = bt;
+        const Opts e = effective(o, *ks);
+        ws = std::max(ws, make_layout(kb, vb, n, num_segments > 0 ? num_segments : 1, e, *ks).total);
+      }
+  *bytes = up((size_t)n * kb) + up((size_t)n * vb) + ws;
+  return DTSORT_OK;
+}
+
+dtsort_status dtsort_autotune(dtsort_handle h, dtsort_op op, const void *keys, const void *values,
+                              const int64_t *offsets, int64_t num_segments, int64_t n,
+                              void *scratch, size_t scratch_bytes, dtsort_stream stream,
+                              dtsort_options *best_out) {
+  if (!h || (int)op < 0 || (int)op >= kOps || n <= 0 || !keys || !scratch ||
+      (has_vals(op) && !values) || (offsets && num_segments <= 0) || ((uintptr_t)scratch % 256))
+    return DTSORT_ERR_INVALID_ARG;
+  size_t need = 0;
+  dtsort_status st = dtsort_autotune_scratch_bytes(h, op, n, offsets ? num_segments : 1, &need);
+  if (st != DTSORT_OK) return st;
+  if (scratch_bytes < need) return DTSORT_ERR_WORKSPACE_TOO_SMALL;
+  KernelShape *ks = nullptr;
+  if (get_shape(h, op, &ks) != cudaSuccess) return DTSORT_ERR_CUDA;
+  const int kb = key_bytes(op), vb = has_vals(op) ? kb : 0;
+  char *w = (char *)scratch;
+  void *ck = w;
+  void *cv = vb ? (void *)(w + up((size_t)n * kb)) : nullptr;
+  void *ws = w + up((size_t)n * kb) + up((size_t)n * vb);
+  const size_t wsb = scratch_bytes - up((size_t)n * kb) - up((size_t)n * vb);
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    return DTSORT_ERR_CUDA;
+  const dtsort_options saved = h->opt;
+  dtsort_options best = saved;
+  double best_ms = 1e30;
+  for (int g : kTuneGamma)
+    for (int cd : kTuneCapDiv)
+      for (int bt : kTuneBlk) {
+        dtsort_options o = saved;
+        o.autotune = 0;
+        o.gamma_max = g;
+        o.finisher_capacity = ks->fin_cap * 2 / cd;
+        o.block_tiles = bt;
+        h->opt = o;
+        double tmin = 1e30;
+        for (int rep = 0; rep < 2 && st == DTSORT_OK; ++rep) {
+          if (cudaMemcpyAsync(ck, keys, (size_t)n * kb, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+              (vb && cudaMemcpyAsync(cv, values, (size_t)n * vb, cudaMemcpyDeviceToDevice, s) !=
+                         cudaSuccess)) {
+            st = DTSORT_ERR_CUDA;
+            break;
+          }
+          cudaEventRecord(e0, s);
+          st = run_sort(h, op, ck, cv, offsets, offsets ? num_segments : 1, n, ws, wsb, s);
+          cudaEventRecord(e1, s);
+          if (cudaEventSynchronize(e1) != cudaSuccess) st = DTSORT_ERR_CUDA;
+          float ms = 0;
+          cudaEventElapsedTime(&ms, e0, e1);
+          tmin = std::min(tmin, (double)ms);
+        }
+        if (st != DTSORT_OK) break;
+        if (tmin < best_ms) {
+          best_ms = tmin;
+          best = o;
+        }
+      }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  h->opt = saved;
+  if (st != DTSORT_OK) return st;
+  // a device-side failure during the trials voids the result
+  int dev_st = 0;
+  if (cudaMemcpy(&dev_st, h->d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return DTSORT_ERR_CUDA;
+  if (dev_st) return (dtsort_status)dev_st;
+  h->opt.gamma_max = best.gamma_max;
+  h->opt.finisher_capacity = best.finisher_capacity;
+  h->opt.block_tiles = best.block_tiles;
+  tune_store(TuneKey{gpu_name(h->device), (int)op, log2_class(n),
+                     log2_class(offsets ? num_segments : 1)},
+             TuneVal{best.gamma_max, best.finisher_capacity, best.block_tiles,
+                     best.sample_log_factor > 0 ? best.sample_log_factor : 1, best_ms});
+  if (best_out) *best_out = h->opt;
   return DTSORT_OK;
 }
 

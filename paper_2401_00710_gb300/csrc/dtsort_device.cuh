@@ -132,7 +132,9 @@ struct Params {
   int64_t target;         // desired bucket size after distribution
   uint64_t seed;
   int32_t sample_factor;  // samples = 2^gamma * L * factor (capped)
-  int32_t debug_fault;    // 1: tile 1 of level 0 never publishes (tests)
+  int32_t debug_fault;    // 1: chunk 1 of level 0 never publishes (tests)
+  int32_t blk_tiles;      // tiles per count-matrix row (block = blk_tiles * TILE)
+  int32_t pad1;
   unsigned long long wait_ns;  // bound of every spin-wait
   Ctl *ctl;
   Seg *segs[2];
@@ -152,6 +154,11 @@ struct Params {
   int *dev_status;
   DevStats *stats;
 };
+
+// The dynamic shared memory of every kernel here.  Phases take their arrays
+// from it by pointer arithmetic only, so the compiler keeps them in the
+// shared address space (32-bit addresses, LDS/STS) instead of generic space.
+extern __shared__ __align__(16) unsigned char dts_smem[];
 
 // ------------------------------------------------------------------ helpers
 __device__ __forceinline__ unsigned long long gtimer() {
@@ -325,16 +332,63 @@ __device__ __forceinline__ unsigned warp_rank_peers(unsigned b, unsigned peers, 
   return old + before;
 }
 
-// Digit width for a subproblem of size s: the fewest levels (of at most
-// gmax bits each) that bring buckets down to about `target` records, bits
-// spread evenly over those levels.
-__device__ __forceinline__ int plan_gamma(int64_t s, int64_t target, int gmax) {
+// Stable rank among this warp's earlier items (in (round, lane) order) with
+// the same bucket.  Every lane ORs its bit into its bucket's shared-memory
+// slot and reads back the set of peers; the lowest peer advances the
+// bucket's running count.  Cost does not grow with the number of distinct
+// buckets or the width of the bucket id.  slot: this warp's slots (zero on
+// entry, zero again on return); wc: this warp's running counts.
+__device__ __forceinline__ unsigned warp_rank_slots(unsigned b, unsigned *slot, uint16_t *wc) {
+  const unsigned lane = threadIdx.x & 31;
+  const unsigned b0 = __shfl_sync(0xffffffffu, b, 0);
+  unsigned peers;
+  if (__all_sync(0xffffffffu, b == b0)) {
+    peers = 0xffffffffu;  // one bucket for the whole warp
+  } else {
+    atomicOr(&slot[b], 1u << lane);
+    __syncwarp();
+    peers = slot[b];
+    __syncwarp();
+  }
+  const unsigned leader = __ffs(peers) - 1;
+  unsigned old = 0;
+  if (lane == leader) {
+    old = wc[b];
+    wc[b] = (uint16_t)(old + __popc(peers));
+    slot[b] = 0;
+  }
+  __syncwarp();
+  old = __shfl_sync(0xffffffffu, old, leader);
+  return old + __popc(peers & lanemask_lt());
+}
+
+// Digit width for a subproblem of size s whose keys have hi unsorted bits:
+// the fewest levels (of at most gmax bits each) that bring buckets down to
+// about `target` records, bits spread evenly over those levels.  When this is
+// the last distribution level (the buckets go to the on-chip base case,
+// which sorts fin_dig bits per pass), a wider digit is taken if it saves a
+// base-case pass.
+__device__ __forceinline__ int plan_gamma(int64_t s, int64_t target, int gmax, int hi,
+                                          int fin_dig) {
   int e = 0;
   while (e < 62 && (target << e) < s) ++e;
   if (e < 1) e = 1;
-  int nlev = (e + gmax - 1) / gmax;
+  const int nlev = (e + gmax - 1) / gmax;
   int g = (e + nlev - 1) / nlev;
-  return g < 1 ? 1 : (g > gmax ? gmax : g);
+  g = g < 1 ? 1 : (g > gmax ? gmax : g);
+  if (nlev == 1 && hi > g) {
+    int best = g, bestp = (hi - g + fin_dig - 1) / fin_dig;
+    // at most 2 more bits: 2^g < 8 * s / target keeps the tables bounded
+    for (int g2 = g + 1; g2 <= gmax && g2 <= hi && g2 <= g + 2; ++g2) {
+      const int p2 = (hi - g2 + fin_dig - 1) / fin_dig;
+      if (p2 < bestp) {
+        best = g2;
+        bestp = p2;
+      }
+    }
+    g = best;
+  }
+  return g;
 }
 
 // ----------------------------------------------------- per-segment tables
@@ -344,35 +398,34 @@ struct SegTables {
   int64_t start, size;
   int32_t hi, seg;
   uint8_t res;
-  int32_t *lid;        // smem, 2^geff + 1
-  K *hkeys;            // smem hash keys
-  uint16_t *hids;      // smem hash ids
 };
 
 // GetBucketId (Alg. 2): heavy keys through H, overflow past the sampled key
-// range, light keys through L by their MSD zone.  Returns nb for nothing.
+// range, light keys through L by their MSD zone.  lid/hk/hid: the tables in
+// shared memory.
 template <typename K>
-__device__ __forceinline__ unsigned bucket_of(const SegTables<K> &T, K key) {
+__device__ __forceinline__ unsigned bucket_of(const SegTables<K> &T, const int32_t *lid,
+                                              const K *hk, const uint16_t *hid, K key) {
   const SegInfo &I = T.info;
   if (I.hbits) {
     const uint32_t cap1 = (1u << I.hbits) - 1u;
     uint32_t s = hash_slot<K>(key, I.hbits);
     while (true) {
-      uint16_t id = T.hids[s];
+      const uint16_t id = hid[s];
       if (id == HEMPTY) break;
-      if (T.hkeys[s] == key) return id;
+      if (hk[s] == key) return id;
       s = (s + 1) & cap1;
     }
   }
-  uint64_t m = (uint64_t)key & lowmask(T.hi);
+  const uint64_t m = (uint64_t)key & lowmask(T.hi);
   if (I.t < 64 && (m >> I.t) != 0) return (unsigned)(I.nb - 1);
-  return (unsigned)T.lid[m >> I.lo];
+  return (unsigned)lid[m >> I.lo];
 }
 
 template <typename K>
-__device__ void load_tables(const Params &P, int seg, int level, SegTables<K> &T,
-                            int32_t *lid_s, K *hk_s, uint16_t *hid_s) {
-  // all threads call; T lives in smem
+__device__ __forceinline__ void load_tables(const Params &P, int seg, int level, SegTables<K> &T,
+                                            int32_t *lid_s, K *hk_s, uint16_t *hid_s) {
+  // all threads call; T lives in shared memory
   if (threadIdx.x == 0) {
     const Seg S = ldcg_obj(&P.segs[level & 1][seg]);
     T.info = ldcg_obj(&P.info[seg]);
@@ -381,9 +434,6 @@ __device__ void load_tables(const Params &P, int seg, int level, SegTables<K> &T
     T.hi = S.hi;
     T.res = S.res;
     T.seg = seg;
-    T.lid = lid_s;
-    T.hkeys = hk_s;
-    T.hids = hid_s;
   }
   __syncthreads();
   const int nz = (1 << (T.info.t - T.info.lo)) + 1;

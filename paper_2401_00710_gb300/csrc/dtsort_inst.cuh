@@ -20,7 +20,7 @@ cudaError_t DTS_CAT(shape_, DTS_NAME)(KernelShape *out) {
   if (e != cudaSuccess) return e;
   out->fin_cap = S::FIN_CAP;
   out->tile = S::TILE;
-  out->blk = S::BLK;
+  out->blk = S::BLK;  // default block (BLK_TILES tiles)
   out->ch = S::CH;
   out->smem = smem;
   out->blocks_per_sm = nb;
@@ -33,6 +33,57 @@ cudaError_t DTS_CAT(launch_, DTS_NAME)(const Params &P, int grid, cudaStream_t s
   Params copy = P;
   void *args[] = {&copy};
   return cudaLaunchCooperativeKernel((const void *)fn, dim3(grid), dim3(NT), args, smem, s);
+}
+
+// One launch per phase; the host reads the control block between levels.
+// ctl_host: pinned host memory for sizeof(Ctl).
+cudaError_t DTS_CAT(launch_split_, DTS_NAME)(const Params &P, int grid, cudaStream_t s,
+                                             void *ctl_host) {
+  auto *fn = dtsort_phase_kernel<DTS_K, DTS_HV>;
+  const size_t smem = smem_bytes<DTS_K, DTS_HV>();
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  Ctl *h = (Ctl *)ctl_host;
+  auto run = [&](int phase, int level, int g) {
+    fn<<<g, NT, smem, s>>>(P, phase, level);
+    return cudaGetLastError();
+  };
+  auto fetch = [&]() {
+    cudaError_t e2 = cudaMemcpyAsync(h, P.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s);
+    if (e2 != cudaSuccess) return e2;
+    return cudaStreamSynchronize(s);
+  };
+  if ((e = run(KP_SEED, 0, grid)) != cudaSuccess) return e;
+  int level = 0;
+  for (; level < MAXLEV; ++level) {
+    if ((e = fetch()) != cudaSuccess) return e;
+    const long long nseg = h->nseg[level & 1];
+    if ((level > 0 && nseg == 0) || h->error) break;
+    if ((e = run(KP_SETUP, level, 1)) != cudaSuccess) return e;
+    if ((e = fetch()) != cudaSuccess) return e;
+    if (h->error) break;
+    if (nseg > 0) {
+      const int ph[] = {KP_SAMPLE, KP_HIST, KP_MSCAN, KP_SCAN, KP_SCATTER};
+      for (int k = 0; k < 5; ++k) {
+        if ((e = run(ph[k], level, grid)) != cudaSuccess) return e;
+        if (ph[k] == KP_MSCAN) {
+          if ((e = fetch()) != cudaSuccess) return e;
+          if (h->error) break;
+        }
+      }
+      if (h->error) break;
+    }
+    if ((e = run(KP_FINISH, level, grid)) != cudaSuccess) return e;
+  }
+  if ((e = run(KP_CLOSE, level, 1)) != cudaSuccess) return e;
+  if ((e = fetch()) != cudaSuccess) return e;
+  for (int l = level - 1; l >= 0 && !h->error; --l) {
+    if (h->lvl_zone[l + 1] == h->lvl_zone[l]) continue;
+    if ((e = run(KP_MERGE_PREP, l, grid)) != cudaSuccess) return e;
+    if ((e = run(KP_MERGE, l, grid)) != cudaSuccess) return e;
+  }
+  return run(KP_STATS, 0, 1);
 }
 
 #if !DTS_HV

@@ -60,10 +60,12 @@ NoallocLayout noalloc_layout(int64_t n) {
   L.target = std::max<int64_t>(16, cap * 7 / 10);
   const int64_t nt = n / L.target + 1;
   L.maxseg = n / (cap + 1) + 2;
-  L.bmax = 3 * nt + L.maxseg + 1024;
-  L.hmax = nt + L.maxseg + 1024;
-  L.zmax = 2 * nt + 2 * L.maxseg + 1024;
-  L.hashmax = 2 * nt + L.maxseg + 1024;
+  // per subproblem 2^gamma < 8 * size / target: buckets <= 1.5 * 2^gamma + 1,
+  // heavy keys <= 2^(gamma-1), light-table entries 2^gamma + 1
+  L.bmax = 12 * nt + L.maxseg + 1024;
+  L.hmax = 4 * nt + L.maxseg + 1024;
+  L.zmax = 8 * nt + 2 * L.maxseg + 1024;
+  L.hashmax = 8 * nt + L.maxseg + 1024;
   L.cwords = (int64_t)dts::NB_HW * (n / Sh::BLK + 1) + L.bmax;
   L.swords = (int64_t)dts::NB_HW * (n / ((int64_t)Sh::BLK * Sh::CH) + 1) + L.bmax;
   L.tmax = 2 * L.bmax + 2 * (n / dts::COPY_CHUNK + 1) + 1 + 4096;
@@ -172,6 +174,7 @@ extern "C" dtsort_status dtsort_u32_kv_noalloc(uint32_t *keys, uint32_t *values,
   P.seed = 1;
   P.sample_factor = 1;
   P.debug_fault = 0;
+  P.blk_tiles = Sh::BLK_TILES;
   P.wait_ns = 2000ull * 1000000ull;
   P.ctl = (dts::Ctl *)(w + L.ctl);
   P.segs[0] = (dts::Seg *)(w + L.segs0);

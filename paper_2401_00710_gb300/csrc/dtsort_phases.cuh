@@ -12,8 +12,9 @@ struct Shape {
   static constexpr int VB = HV ? (int)sizeof(K) : 0;
   static constexpr int ITEMS = KB == 4 ? 16 : 8;        // scatter items / thread
   static constexpr int TILE = NT * ITEMS;
-  static constexpr int FIN_BYTES = 96 * 1024;           // base-case data buffers
-  static constexpr int FIN_CAP = FIN_BYTES / (2 * (KB + VB));
+  static constexpr int FIN_CAP = (96 * 1024) / (2 * (KB + VB)) < 6144
+                                      ? (96 * 1024) / (2 * (KB + VB)) : 6144;
+  static constexpr int FIN_BYTES = 2 * FIN_CAP * (KB + VB);  // base-case buffers
   static constexpr int FIN_IT = FIN_CAP / NT;           // base-case items / thread
   static constexpr int STAGE = TILE * KB;               // scatter staging (keys or values)
   static constexpr int BLK_TILES = 4;                   // tiles per count-matrix row
@@ -21,14 +22,32 @@ struct Shape {
   static constexpr int CH = 32;                         // rows per look-back chunk
 };
 
+// One record of the on-chip base case: key, and the value next to it, so that
+// a pass moves each record with one shared-memory load and one store.
+template <typename K, bool HV>
+struct Rec {
+  K k;
+};
+template <>
+struct alignas(8) Rec<uint32_t, true> {
+  uint32_t k, v;
+};
+template <>
+struct alignas(16) Rec<uint64_t, true> {
+  uint64_t k, v;
+};
+
+// Hands out 16-byte aligned arrays of the kernel's dynamic shared memory, by
+// pointer arithmetic on dts_smem (the shared address space stays visible).
 struct Carve {
-  unsigned char *p;
-  __device__ explicit Carve(unsigned char *q) : p(q) {}
+  size_t off = 0;
+  __device__ __forceinline__ Carve() {}
   template <typename T>
-  __device__ T *take(size_t n) {
-    uintptr_t a = ((uintptr_t)p + 15) & ~(uintptr_t)15;
-    p = (unsigned char *)(a + n * sizeof(T));
-    return (T *)a;
+  __device__ __forceinline__ T *take(size_t n) {
+    off = (off + 15) & ~(size_t)15;
+    T *r = reinterpret_cast<T *>(dts_smem + off);
+    off += n * sizeof(T);
+    return r;
   }
 };
 
@@ -40,10 +59,11 @@ constexpr size_t smem_bytes() {
   sc += 64 + sizeof(SegTables<K>);
   sc += 16 + 4 * ((1 << GAMMA_HW) + 1);            // lid
   sc += 16 + sizeof(K) * HASH_HW + 16 + 2 * HASH_HW;  // hash
-  sc += 16 + (size_t)S::STAGE;                     // key / value staging
-  sc += 16 + 2 * (size_t)S::TILE;                  // bucket of each staged slot
   sc += 16 + 2 * (size_t)NWARP * NB_PAD;           // warp counters
-  sc += 16 + 4 * NB_PAD * 2 + 16 + 16 * NB_PAD;    // tile counts/offsets, bases
+  sc += 4 * (16 + 4 * NB_PAD);                     // tile counts/offsets, bases
+  const size_t stage_b = (size_t)S::TILE * sizeof(K) + 4 * (size_t)S::TILE;
+  const size_t slot_b = 4 * (size_t)NWARP * NB_PAD;
+  sc += 16 + (slot_b > stage_b ? slot_b : stage_b);  // rank slots / staged tile
   sc += 16 + 8 * (NWARP + 1) + 256;
   // base case
   size_t fin = 0;
@@ -146,7 +166,7 @@ __device__ void phase_setup(const Params &P, int level, unsigned char *smem) {
   Ctl *c = P.ctl;
   const int p = level & 1;
   const int64_t nseg = min(ld_cg64(&c->nseg[p]), (long long)P.maxseg);
-  long long *sh = (long long *)smem;  // NWARP+1 scratch
+  long long *sh = (long long *)dts_smem;  // NWARP+1 scratch
   int64_t cr_blk = 0, cr_chk = 0, cr_b = 0, cr_h = 0, cr_z = 0, cr_hash = 0, cr_c = 0,
           cr_st = 0, cr_rec = 0;
   for (int64_t base = 0; base < nseg; base += NT) {
@@ -156,8 +176,9 @@ __device__ void phase_setup(const Params &P, int level, unsigned char *smem) {
     if (i < nseg) {
       const Seg s = ldcg_obj(&P.segs[p][i]);
       sz = s.size;
-      g = plan_gamma(s.size, P.target, P.gamma_max);
-      nblk = (s.size + S::BLK - 1) / S::BLK;
+      g = plan_gamma(s.size, P.target, P.gamma_max, s.hi, FIN_DIG);
+      const int64_t blk = (int64_t)P.blk_tiles * S::TILE;
+      nblk = (s.size + blk - 1) / blk;
       nchk = (nblk + S::CH - 1) / S::CH;
       nbm = (1 << g) + (1 << (g - 1)) + 1;
       hm = 1 << (g - 1);
@@ -225,7 +246,7 @@ __device__ void phase_sample(const Params &P, int level, unsigned char *smem) {
   const int p = level & 1;
   const int64_t nseg = min(ld_cg64(&c->nseg[p]), (long long)P.maxseg);
   const K *src = (const K *)P.keys[level & 1];
-  Carve cv(smem);
+  Carve cv;
   K *Ssm = cv.take<K>(SMAX);
   K *hv = cv.take<K>(SMAX / 2 + 8);
   K *hk = cv.take<K>(HASH_HW);
@@ -374,7 +395,7 @@ __device__ void phase_hist(const Params &P, int level, unsigned char *smem) {
   const int64_t nblocks = ld_cg64(&c->nblocks);
   if (nblocks == 0) return;
   const K *src = (const K *)P.keys[level & 1];
-  Carve cv(smem);
+  Carve cv;
   SegTables<K> &T = *cv.take<SegTables<K>>(1);
   int32_t *lid_s = cv.take<int32_t>((1 << GAMMA_HW) + 1);
   K *hk_s = cv.take<K>(HASH_HW);
@@ -392,6 +413,9 @@ __device__ void phase_hist(const Params &P, int level, unsigned char *smem) {
       cur = s;
     }
     const int nb = T.info.nb;
+    const int lo = T.info.lo;
+    const unsigned gmask = (1u << (T.info.t - T.info.lo)) - 1u;
+    const bool fast = T.info.hbits == 0 && T.info.t >= T.hi;
     const int64_t lr = r - T.info.blk0;
     if (lr % S::CH == 0) {  // this chunk's look-back status starts empty
       const int64_t row = T.info.soff + (lr / S::CH) * nb;
@@ -399,9 +423,9 @@ __device__ void phase_hist(const Params &P, int level, unsigned char *smem) {
     }
     for (int b = threadIdx.x; b < NB_PAD; b += NT) cnt[b] = 0;
     __syncthreads();
-    const int64_t b0 = T.start + lr * S::BLK;
+    const int64_t b0 = T.start + lr * (int64_t)P.blk_tiles * S::TILE;
     const int64_t brem = T.start + T.size - b0;
-    for (int sub = 0; sub < S::BLK_TILES; ++sub) {
+    for (int sub = 0; sub < P.blk_tiles; ++sub) {
       const int64_t tb = (int64_t)sub * S::TILE;
       if (tb >= brem) break;
       const int tn = brem - tb < S::TILE ? (int)(brem - tb) : S::TILE;
@@ -412,10 +436,18 @@ __device__ void phase_hist(const Params &P, int level, unsigned char *smem) {
         const int i = w * 32 * S::ITEMS + j * 32 + lane;
         key[j] = i < tn ? ld_key<K>(ts + i) : (K)0;
       }
+      if (fast) {
 #pragma unroll
-      for (int j = 0; j < S::ITEMS; ++j) {
-        const int i = w * 32 * S::ITEMS + j * 32 + lane;
-        if (i < tn) atomicAdd(&cnt[bucket_of<K>(T, key[j])], 1u);
+        for (int j = 0; j < S::ITEMS; ++j) {
+          const int i = w * 32 * S::ITEMS + j * 32 + lane;
+          if (i < tn) atomicAdd(&cnt[(unsigned)((uint64_t)key[j] >> lo) & gmask], 1u);
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < S::ITEMS; ++j) {
+          const int i = w * 32 * S::ITEMS + j * 32 + lane;
+          if (i < tn) atomicAdd(&cnt[bucket_of<K>(T, lid_s, hk_s, hid_s, key[j])], 1u);
+        }
       }
     }
     __syncthreads();
@@ -436,8 +468,8 @@ __device__ void phase_mscan(const Params &P, int level, unsigned char *smem) {
   Ctl *c = P.ctl;
   const int64_t nseg = min(ld_cg64(&c->nseg[level & 1]), (long long)P.maxseg);
   const int64_t nchunks = ld_cg64(&c->nchunks);
-  long long *chunk_sh = (long long *)smem;
-  SegInfo *Is = (SegInfo *)(smem + 16);
+  long long *chunk_sh = (long long *)dts_smem;
+  SegInfo *Is = (SegInfo *)(dts_smem + 16);
   while (true) {
     if (threadIdx.x == 0) *chunk_sh = atomic_add_ll(&c->chunk_ctr, 1ll);
     __syncthreads();
@@ -506,7 +538,7 @@ __device__ void phase_scan(const Params &P, int level, unsigned char *smem) {
   const int p = level & 1;
   const int64_t nseg = min(ld_cg64(&c->nseg[p]), (long long)P.maxseg);
   const int srcb = level & 1, dstb = srcb ^ 1;
-  Carve cv(smem);
+  Carve cv;
   long long *cntv = cv.take<long long>(NB_PAD);
   long long *excl = cv.take<long long>(NB_PAD + 1);
   int32_t *lid_s = cv.take<int32_t>((1 << GAMMA_HW) + 1);
@@ -582,9 +614,10 @@ __device__ void phase_scan(const Params &P, int level, unsigned char *smem) {
 
 // ---------------------------------------------------------------- scatter
 // Stable counting-sort scatter: block r writes bucket b's records starting at
-// bstart[b] + X[r][b]; inside the block, tiles of TILE records are ranked by
-// warp match in input order and staged in shared memory in bucket order so
-// that each bucket's run is written contiguously.
+// bstart[b] + X[r][b]; inside the block, tiles of TILE records are ranked per
+// warp in input order and staged in shared memory in bucket order so that
+// each bucket's run is written contiguously.  A subproblem without heavy keys
+// whose digit reaches its top unsorted bit needs no table: bucket = digit.
 template <typename K, bool HV>
 __device__ void phase_scatter(const Params &P, int level, unsigned char *smem) {
   using S = Shape<K, HV>;
@@ -596,21 +629,27 @@ __device__ void phase_scatter(const Params &P, int level, unsigned char *smem) {
   K *dst = (K *)P.keys[dstb];
   const K *vsrc = HV ? (const K *)P.vals[srcb] : nullptr;
   K *vdst = HV ? (K *)P.vals[dstb] : nullptr;
-  Carve cv(smem);
+  Carve cv;
   SegTables<K> &T = *cv.take<SegTables<K>>(1);
   int32_t *lid_s = cv.take<int32_t>((1 << GAMMA_HW) + 1);
   K *hk_s = cv.take<K>(HASH_HW);
   uint16_t *hid_s = cv.take<uint16_t>(HASH_HW);
-  K *stage = cv.take<K>(S::TILE);
-  uint16_t *bid = cv.take<uint16_t>(S::TILE);
   uint16_t *wcnt = cv.take<uint16_t>(NWARP * NB_PAD);
   unsigned *tcnt = cv.take<unsigned>(NB_PAD);
   unsigned *toff = cv.take<unsigned>(NB_PAD);
-  long long *gbase = cv.take<long long>(NB_PAD);
-  long long *base = cv.take<long long>(NB_PAD);
+  unsigned *gbase = cv.take<unsigned>(NB_PAD);
+  unsigned *base = cv.take<unsigned>(NB_PAD);
   unsigned *sh = cv.take<unsigned>(NWARP + 1);
+  // ranking slots and the staged tile share one area (never live together)
+  constexpr int AREA = (4 * NWARP * NB_PAD > S::TILE * (int)sizeof(K) + 4 * S::TILE)
+                           ? 4 * NWARP * NB_PAD : S::TILE * (int)sizeof(K) + 4 * S::TILE;
+  unsigned char *area = cv.take<unsigned char>(AREA);
+  unsigned *slots = (unsigned *)area;
+  K *stage = (K *)area;
+  unsigned *dest = (unsigned *)(area + S::TILE * sizeof(K));  // offset in the subproblem
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   uint16_t *mywc = wcnt + w * NB_PAD;
+  unsigned *myslot = slots + w * NB_PAD;
   const int64_t r0 = nblocks * blockIdx.x / gridDim.x;
   const int64_t r1 = nblocks * (blockIdx.x + 1) / gridDim.x;
   int cur = -1;
@@ -622,36 +661,52 @@ __device__ void phase_scatter(const Params &P, int level, unsigned char *smem) {
       cur = s;
     }
     const int nb = T.info.nb;
+    const int lo = T.info.lo;
+    const unsigned gmask = (1u << (T.info.t - T.info.lo)) - 1u;
+    const bool fast = T.info.hbits == 0 && T.info.t >= T.hi;
     const int64_t lr = r - T.info.blk0;
     const unsigned *X = P.cmat + T.info.coff + lr * nb;
     for (int b = threadIdx.x; b < nb; b += NT)
-      base[b] = __ldcg((const long long *)&P.bstart[T.info.boff + b]) + (long long)__ldcg(X + b);
-    const int64_t b0 = T.start + lr * S::BLK;
+      base[b] = (unsigned)(__ldcg((const long long *)&P.bstart[T.info.boff + b]) - T.start) +
+                __ldcg(X + b);
+    const int64_t b0 = T.start + lr * (int64_t)P.blk_tiles * S::TILE;
     const int64_t brem = T.start + T.size - b0;
-    const int64_t lo_ok = T.start, hi_ok = T.start + T.size;
-    for (int sub = 0; sub < S::BLK_TILES; ++sub) {
+    K *dseg = dst + T.start;
+    K *vdseg = HV ? vdst + T.start : nullptr;
+    const unsigned seg_size = (unsigned)T.size;
+    for (int sub = 0; sub < P.blk_tiles; ++sub) {
       const int64_t tb = (int64_t)sub * S::TILE;
       if (tb >= brem) break;
       const int tn = brem - tb < S::TILE ? (int)(brem - tb) : S::TILE;
       const int64_t tbase = b0 + tb;
-      for (int i = threadIdx.x; i < NWARP * NB_PAD; i += NT) wcnt[i] = 0;
-      __syncthreads();
-      // keys in, bucket ids, warp ranks (item order = input order)
+      {
+        uint4 *z = (uint4 *)wcnt;
+        for (int i = threadIdx.x; i < NWARP * NB_PAD * 2 / 16; i += NT) z[i] = make_uint4(0, 0, 0, 0);
+        uint4 *z2 = (uint4 *)slots;
+        for (int i = threadIdx.x; i < NWARP * NB_PAD * 4 / 16; i += NT) z2[i] = make_uint4(0, 0, 0, 0);
+      }
       K key[S::ITEMS];
-      unsigned br[S::ITEMS];  // bucket << 16 | rank within warp
+      unsigned br[S::ITEMS];  // bucket << 16 | rank within warp, later the slot
 #pragma unroll
       for (int j = 0; j < S::ITEMS; ++j) {
         const int i = w * 32 * S::ITEMS + j * 32 + lane;
         key[j] = i < tn ? ld_key<K>(src + tbase + i) : (K)0;
       }
-      const int nbits = 32 - __clz(nb);  // bits of ids 0..nb (nb = dummy)
+      __syncthreads();
+      if (fast) {
 #pragma unroll
-      for (int j = 0; j < S::ITEMS; ++j) {
-        const int i = w * 32 * S::ITEMS + j * 32 + lane;
-        unsigned b = (unsigned)nb;
-        if (i < tn) b = bucket_of<K>(T, key[j]);
-        const unsigned rk = warp_rank_peers(b, warp_peers(b, nbits), mywc);
-        br[j] = (b << 16) | rk;
+        for (int j = 0; j < S::ITEMS; ++j) {
+          const int i = w * 32 * S::ITEMS + j * 32 + lane;
+          const unsigned b = i < tn ? ((unsigned)((uint64_t)key[j] >> lo) & gmask) : (unsigned)nb;
+          br[j] = (b << 16) | warp_rank_slots(b, myslot, mywc);
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < S::ITEMS; ++j) {
+          const int i = w * 32 * S::ITEMS + j * 32 + lane;
+          const unsigned b = i < tn ? bucket_of<K>(T, lid_s, hk_s, hid_s, key[j]) : (unsigned)nb;
+          br[j] = (b << 16) | warp_rank_slots(b, myslot, mywc);
+        }
       }
       __syncthreads();
       // per bucket: exclusive prefix over warps, tile total
@@ -676,9 +731,10 @@ __device__ void phase_scatter(const Params &P, int level, unsigned char *smem) {
       }
       __syncthreads();
       for (int b = threadIdx.x; b < nb; b += NT) {
-        gbase[b] = base[b] - (long long)toff[b];
+        gbase[b] = base[b] - toff[b];
         base[b] += tcnt[b];
       }
+      __syncthreads();
       // stage keys in bucket order, then write each bucket's run contiguously;
       // br[j] becomes the item's slot in the staged tile
 #pragma unroll
@@ -688,7 +744,7 @@ __device__ void phase_scatter(const Params &P, int level, unsigned char *smem) {
           const unsigned b = br[j] >> 16;
           const unsigned pj = toff[b] + wcnt[w * NB_PAD + b] + (br[j] & 0xFFFFu);
           stage[pj] = key[j];
-          bid[pj] = (uint16_t)b;
+          dest[pj] = gbase[b] + pj;
           br[j] = pj;
         }
       }
@@ -703,8 +759,8 @@ __device__ void phase_scatter(const Params &P, int level, unsigned char *smem) {
       }
       __syncthreads();
       for (int q = threadIdx.x; q < tn; q += NT) {
-        const int64_t d = gbase[bid[q]] + q;
-        if (d >= lo_ok && d < hi_ok) dst[d] = stage[q];
+        const unsigned d = dest[q];
+        if (d < seg_size) dseg[d] = stage[q];
         else latch(P, ERR_INTERNAL);
       }
       if constexpr (HV) {
@@ -716,8 +772,8 @@ __device__ void phase_scatter(const Params &P, int level, unsigned char *smem) {
         }
         __syncthreads();
         for (int q = threadIdx.x; q < tn; q += NT) {
-          const int64_t d = gbase[bid[q]] + q;
-          if (d >= lo_ok && d < hi_ok) vdst[d] = stage[q];
+          const unsigned d = dest[q];
+          if (d < seg_size) vdseg[d] = stage[q];
         }
       }
       __syncthreads();
@@ -731,17 +787,17 @@ __device__ void phase_finish(const Params &P, int level, unsigned char *smem) {
   using S = Shape<K, HV>;
   Ctl *c = P.ctl;
   const int64_t ntasks = min(ld_cg64(&c->ntasks), (long long)P.tmax);
-  Carve cv(smem);
-  K *ka = cv.take<K>(S::FIN_CAP);
-  K *kb = cv.take<K>(S::FIN_CAP);
-  K *va = HV ? cv.take<K>(S::FIN_CAP) : nullptr;
-  K *vb = HV ? cv.take<K>(S::FIN_CAP) : nullptr;
+  using RecT = Rec<K, HV>;
+  Carve cv;
+  RecT *ra = cv.take<RecT>(S::FIN_CAP);
+  RecT *rb = cv.take<RecT>(S::FIN_CAP);
   uint16_t *wcnt = cv.take<uint16_t>(NWARP * FIN_NB);
   unsigned *dcnt = cv.take<unsigned>(FIN_NB);
   unsigned *doff = cv.take<unsigned>(FIN_NB);
   unsigned *sh = cv.take<unsigned>(NWARP + 1);
   long long *task_sh = cv.take<long long>(1);
   int *flag_sh = cv.take<int>(1);
+  static_assert(sizeof(RecT) * S::FIN_CAP >= 4 * NWARP * FIN_NB, "slots fit in a buffer");
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   uint16_t *mywc = wcnt + w * FIN_NB;
   long long my_recs = 0, my_tasks = 0, my_copy = 0;
@@ -766,48 +822,49 @@ __device__ void phase_finish(const Params &P, int level, unsigned char *smem) {
     }
     const int n = (int)tk.size;
     {
-      K kr[S::FIN_IT];
+      RecT rr[S::FIN_IT];
 #pragma unroll
       for (int j = 0; j < S::FIN_IT; ++j) {
         const int i = j * NT + threadIdx.x;
-        if (i < n) kr[j] = ld_key<K>(ksrc + tk.start + i);
+        if (i < n) {
+          rr[j].k = ld_key<K>(ksrc + tk.start + i);
+          if constexpr (HV) rr[j].v = ld_key<K>(vsrc + tk.start + i);
+        }
       }
 #pragma unroll
       for (int j = 0; j < S::FIN_IT; ++j) {
         const int i = j * NT + threadIdx.x;
-        if (i < n) ka[i] = kr[j];
-      }
-      if constexpr (HV) {
-#pragma unroll
-        for (int j = 0; j < S::FIN_IT; ++j) {
-          const int i = j * NT + threadIdx.x;
-          if (i < n) kr[j] = ld_key<K>(vsrc + tk.start + i);
-        }
-#pragma unroll
-        for (int j = 0; j < S::FIN_IT; ++j) {
-          const int i = j * NT + threadIdx.x;
-          if (i < n) va[i] = kr[j];
-        }
+        if (i < n) ra[i] = rr[j];
       }
     }
     __syncthreads();
-    K *kin = ka, *kout = kb, *vin = va, *vout = vb;
+    RecT *rin = ra, *rout = rb;
     const int passes = (tk.hi + FIN_DIG - 1) / FIN_DIG;
+    // every warp ranks R consecutive rounds of 32 items (warp w covers
+    // [32 R w, 32 R (w+1)) of the current order), R as small as n allows
+    const int R = (n + NT - 1) / NT;
     for (int q = 0; q < passes; ++q) {
       const int shift = q * FIN_DIG;
       const int bits = tk.hi - shift < FIN_DIG ? tk.hi - shift : FIN_DIG;
       const unsigned dmask = (1u << bits) - 1u;
-      for (int i = threadIdx.x; i < NWARP * FIN_NB; i += NT) wcnt[i] = 0;
+      unsigned *fslots = (unsigned *)rout;  // rout is free until the scatter
+      {
+        uint4 *z = (uint4 *)wcnt;
+        for (int i = threadIdx.x; i < NWARP * FIN_NB * 2 / 16; i += NT) z[i] = make_uint4(0, 0, 0, 0);
+        uint4 *z2 = (uint4 *)fslots;
+        for (int i = threadIdx.x; i < NWARP * FIN_NB * 4 / 16; i += NT) z2[i] = make_uint4(0, 0, 0, 0);
+      }
       __syncthreads();
+      unsigned *myfs = fslots + w * FIN_NB;
       unsigned dr[S::FIN_IT];
 #pragma unroll
       for (int j = 0; j < S::FIN_IT; ++j) {
-        const int i = w * 32 * S::FIN_IT + j * 32 + lane;
+        const int i = w * 32 * R + j * 32 + lane;
         dr[j] = 0xFFFFFFFFu;
-        if (w * 32 * S::FIN_IT + j * 32 < n) {  // warp-uniform
+        if (j < R && w * 32 * R + j * 32 < n) {  // warp-uniform
           unsigned d = 1u << FIN_DIG;  // dummy digit
-          if (i < n) d = (unsigned)((uint64_t)kin[i] >> shift) & dmask;
-          const unsigned r = warp_rank_peers(d, warp_peers_fixed<FIN_DIG + 1>(d), mywc);
+          if (i < n) d = (unsigned)((uint64_t)rin[i].k >> shift) & dmask;
+          const unsigned r = warp_rank_slots(d, myfs, mywc);
           dr[j] = (d << 16) | r;
         }
       }
@@ -836,21 +893,22 @@ __device__ void phase_finish(const Params &P, int level, unsigned char *smem) {
       if (*flag_sh) continue;  // pass would be the identity
 #pragma unroll
       for (int j = 0; j < S::FIN_IT; ++j) {
-        const int i = w * 32 * S::FIN_IT + j * 32 + lane;
-        if (i < n) {
+        const int i = w * 32 * R + j * 32 + lane;
+        if (j < R && i < n) {
           const unsigned d = dr[j] >> 16;
           const unsigned pp = doff[d] + wcnt[w * FIN_NB + d] + (dr[j] & 0xFFFFu);
-          kout[pp] = kin[i];
-          if constexpr (HV) vout[pp] = vin[i];
+          rout[pp] = rin[i];
         }
       }
       __syncthreads();
-      K *tk_ = kin; kin = kout; kout = tk_;
-      if constexpr (HV) { K *tv = vin; vin = vout; vout = tv; }
+      RecT *t_ = rin;
+      rin = rout;
+      rout = t_;
     }
     for (int i = threadIdx.x; i < n; i += NT) {
-      kdst[tk.start + i] = kin[i];
-      if constexpr (HV) vdst[tk.start + i] = vin[i];
+      const RecT x = rin[i];
+      kdst[tk.start + i] = x.k;
+      if constexpr (HV) vdst[tk.start + i] = x.v;
     }
     __syncthreads();
     my_recs += n;
@@ -873,7 +931,7 @@ __device__ void phase_merge_prep(const Params &P, int level, unsigned char *smem
   Ctl *c = P.ctl;
   const int64_t z0 = min(ld_cg64(&c->lvl_zone[level]), (long long)P.mhmax);
   const int64_t z1 = min(ld_cg64(&c->lvl_zone[level + 1]), (long long)P.mhmax);
-  long long *sh = (long long *)smem;
+  long long *sh = (long long *)dts_smem;
   for (int64_t zi = z0 + blockIdx.x; zi < z1; zi += gridDim.x) {
     const MZone Z = ldcg_obj(&P.zones[zi]);
     const K *B0 = (const K *)P.keys[Z.obuf ^ 1] + Z.zs;
@@ -904,7 +962,7 @@ __device__ void phase_merge(const Params &P, int level, unsigned char *smem) {
   const int64_t z1 = min(ld_cg64(&c->lvl_zone[level + 1]), (long long)P.mhmax);
   const int64_t c0 = (int64_t)__ldcg(&c->lvl_chunk[level]);
   const int64_t c1 = (int64_t)__ldcg(&c->lvl_chunk[level + 1]);
-  Carve cv(smem);
+  Carve cv;
   long long *hs = cv.take<long long>(HASH_HW / 2 + 1);
   long long *hz = cv.take<long long>(HASH_HW / 2 + 1);
   long long *hp = cv.take<long long>(HASH_HW / 2 + 1);
@@ -980,9 +1038,47 @@ __device__ __forceinline__ void tick(const Params &P, int kind) {
   }
 }
 
+// After the last level: record the level count and the merge zones' end.
+__device__ __forceinline__ void close_levels(const Params &P, int level) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    Ctl *c = P.ctl;
+    c->nlevels = level;
+    const unsigned long long za = __ldcg(&c->zone_alloc);
+    c->lvl_zone[level] = (long long)(za >> 40);
+    c->lvl_chunk[level] = za & ((1ull << 40) - 1);
+  }
+}
+
+__device__ __forceinline__ void write_stats(const Params &P, unsigned long long tbeg) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    Ctl *c = P.ctl;
+    DevStats *d = P.stats;
+    d->levels = c->nlevels;
+    d->status = *(volatile int *)&c->error;
+    for (int l = 0; l < 16; ++l) {
+      d->segments[l] = ld_cg64(&c->st_segments[l]);
+      d->records[l] = ld_cg64(&c->st_records[l]);
+      d->heavy_keys[l] = ld_cg64(&c->st_heavy_keys[l]);
+      d->heavy_records[l] = ld_cg64(&c->st_heavy_records[l]);
+      d->overflow_records[l] = ld_cg64(&c->st_overflow[l]);
+    }
+    d->finisher_tasks = ld_cg64(&c->st_fin_tasks);
+    d->finisher_records = ld_cg64(&c->st_fin_records);
+    d->copy_records = ld_cg64(&c->st_copy_records);
+    d->merge_zones = (int64_t)(__ldcg(&c->zone_alloc) >> 40);
+    d->merge_records = ld_cg64(&c->st_merge_records);
+    d->learned_fixup_records = 0;
+    d->learned_fixup_steps = 0;
+    d->learned_cv = 0;
+    d->learned_mom = 0;
+    for (int k = 0; k < 7; ++k) d->phase_ms[k] = (double)c->t_phase[k] * 1e-6;
+    d->phase_ms[7] = tbeg ? (double)(gtimer() - tbeg) * 1e-6 : 0.0;
+  }
+}
+
 template <typename K, bool HV>
 __global__ void __launch_bounds__(NT, 2) dtsort_kernel(const Params P) {
-  extern __shared__ __align__(16) unsigned char smem[];
+  unsigned char *smem = dts_smem;
   Ctl *c = P.ctl;
   if (blockIdx.x == 0 && threadIdx.x == 0) c->t_last = gtimer();
   const unsigned long long tbeg = gtimer();
@@ -1021,12 +1117,7 @@ __global__ void __launch_bounds__(NT, 2) dtsort_kernel(const Params P) {
     grid_sync(P);
     tick(P, PH_FINISH);
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    c->nlevels = level;
-    const unsigned long long za = __ldcg(&c->zone_alloc);
-    c->lvl_zone[level] = (long long)(za >> 40);
-    c->lvl_chunk[level] = za & ((1ull << 40) - 1);
-  }
+  close_levels(P, level);
   grid_sync(P);
   for (int l = level - 1; l >= 0; --l) {
     if (*(volatile int *)&c->err_snap) break;
@@ -1037,29 +1128,34 @@ __global__ void __launch_bounds__(NT, 2) dtsort_kernel(const Params P) {
     grid_sync(P);
     tick(P, PH_MERGE);
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    DevStats *d = P.stats;
-    const int L = c->nlevels;
-    d->levels = L;
-    d->status = *(volatile int *)&c->error;
-    for (int l = 0; l < 16; ++l) {
-      d->segments[l] = ld_cg64(&c->st_segments[l]);
-      d->records[l] = ld_cg64(&c->st_records[l]);
-      d->heavy_keys[l] = ld_cg64(&c->st_heavy_keys[l]);
-      d->heavy_records[l] = ld_cg64(&c->st_heavy_records[l]);
-      d->overflow_records[l] = ld_cg64(&c->st_overflow[l]);
-    }
-    d->finisher_tasks = ld_cg64(&c->st_fin_tasks);
-    d->finisher_records = ld_cg64(&c->st_fin_records);
-    d->copy_records = ld_cg64(&c->st_copy_records);
-    d->merge_zones = (int64_t)(__ldcg(&c->zone_alloc) >> 40);
-    d->merge_records = ld_cg64(&c->st_merge_records);
-    d->learned_fixup_records = 0;
-    d->learned_fixup_steps = 0;
-    d->learned_cv = 0;
-    d->learned_mom = 0;
-    for (int k = 0; k < 7; ++k) d->phase_ms[k] = (double)c->t_phase[k] * 1e-6;
-    d->phase_ms[7] = (double)(gtimer() - tbeg) * 1e-6;
+  write_stats(P, tbeg);
+}
+
+// The same phases as separate launches (one phase per launch, the level loop
+// driven by the host).  A profiling aid: every phase shows up as its own
+// kernel launch; the persistent kernel above is the product path.
+enum {
+  KP_SEED = 0, KP_SETUP, KP_SAMPLE, KP_HIST, KP_MSCAN, KP_SCAN, KP_SCATTER, KP_FINISH,
+  KP_CLOSE, KP_MERGE_PREP, KP_MERGE, KP_STATS
+};
+
+template <typename K, bool HV>
+__global__ void __launch_bounds__(NT, 2) dtsort_phase_kernel(const Params P, int phase, int level) {
+  unsigned char *smem = dts_smem;
+  switch (phase) {
+    case KP_SEED: phase_seed<K, HV>(P); break;
+    case KP_SETUP: if (blockIdx.x == 0) phase_setup<K, HV>(P, level, smem); break;
+    case KP_SAMPLE: phase_sample<K, HV>(P, level, smem); break;
+    case KP_HIST: phase_hist<K, HV>(P, level, smem); break;
+    case KP_MSCAN: phase_mscan<K, HV>(P, level, smem); break;
+    case KP_SCAN: phase_scan<K, HV>(P, level, smem); break;
+    case KP_SCATTER: phase_scatter<K, HV>(P, level, smem); break;
+    case KP_FINISH: phase_finish<K, HV>(P, level, smem); break;
+    case KP_CLOSE: close_levels(P, level); break;
+    case KP_MERGE_PREP: phase_merge_prep<K, HV>(P, level, smem); break;
+    case KP_MERGE: phase_merge<K, HV>(P, level, smem); break;
+    case KP_STATS: write_stats(P, 0); break;
+    default: break;
   }
 }
 
@@ -1070,8 +1166,7 @@ __global__ void __launch_bounds__(NT) sample_debug_kernel(const K *keys, int64_t
                                                           int64_t size, int hi, uint64_t seed,
                                                           int64_t m, int64_t L, uint64_t *heavy_out,
                                                           int64_t *nheavy_out, uint64_t *max_out) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  Carve cv(smem);
+  Carve cv;
   K *Ssm = cv.take<K>(SMAX);
   long long *sh = cv.take<long long>(NWARP + 1);
   int M = 1;

@@ -155,6 +155,17 @@ def test_options_do_not_change_output(G, opts):
         check(G, keys, vals)
 
 
+def test_phase_launch_mode_matches(G):
+    # one launch per phase (profiling aid) runs the same phases
+    n = 1_500_000
+    for name in ("zipf1.2", "uniform"):
+        keys = gen.family(name, n, np.uint32, seed=14)
+        vals = gen.iota(n, np.uint32)
+        G.set_options(launch_mode=1)
+        st = check(G, keys, vals)
+        assert st["levels"] >= 1
+
+
 # --------------------------------------------------------------- segmented
 @pytest.mark.parametrize("dtype", [np.uint32, np.uint64])
 def test_segmented(G, dtype):
