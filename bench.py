@@ -56,6 +56,7 @@ def parse():
                     help="segmented: capture the call once, replay it per step")
     ap.add_argument("--baseline-calls", action="store_true",
                     help="segmented: also time one dtsort_u32_kv call per array")
+    ap.add_argument("--bucketing", default="digit", choices=["digit", "learned"])
     ap.add_argument("--autotune", action="store_true",
                     help="run the autotuner on the workload first and use its choice")
     return ap.parse_args()
@@ -190,6 +191,18 @@ def run_reference(args):
     return 0
 
 
+def device_error_text(h, st):
+    """Status text plus the first failed internal check, if one was recorded."""
+    text = dts.status_string(st)
+    if st == dts.DTSORT_ERR_INTERNAL:
+        try:
+            d = dts.dtsort_get_stats(h).as_dict()
+            text += " (check site %d, values %s)" % (d["check_site"], d["check_values"])
+        except Exception:  # the context itself may be gone
+            pass
+    return text
+
+
 def run_ours(args):
     import torch
 
@@ -221,9 +234,11 @@ def run_ours(args):
     op = {"u32kv": dts.DTSORT_OP_U32_KV, "u32": dts.DTSORT_OP_U32,
           "u64kv": dts.DTSORT_OP_U64_KV, "u64": dts.DTSORT_OP_U64}[args.op]
     h = dts.dtsort_create(local)
-    if args.launch_mode:
+    if args.launch_mode or args.bucketing == "learned":
         o = dts.dtsort_get_options(h)
         o.launch_mode = args.launch_mode
+        if args.bucketing == "learned":
+            o.bucketing = dts.DTSORT_BUCKETING_LEARNED
         dts.dtsort_set_options(h, o)
     wsb = dts.dtsort_workspace_bytes(h, op, n)
     ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
@@ -256,7 +271,7 @@ def run_ours(args):
         sort_once(k.data_ptr(), v.data_ptr() if has_v else None)
     st = dts.dtsort_last_device_error(h, sp)
     if st != 0:
-        raise RuntimeError("device: " + dts.status_string(st))
+        raise RuntimeError("device: " + device_error_text(h, st))
     # ---- timed: K sorts, CUDA events around each sort on its stream ----
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
@@ -270,7 +285,7 @@ def run_ours(args):
         barrier()
     st = dts.dtsort_last_device_error(h, sp)
     if st != 0:
-        raise RuntimeError("device: " + dts.status_string(st))
+        raise RuntimeError("device: " + device_error_text(h, st))
     ms = [a.elapsed_time(b) for a, b in ev]
     ms_step = sum(ms) / len(ms)
     if world > 1:
@@ -315,8 +330,9 @@ def run_ours(args):
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": args.op, "data": "synthetic",
-        "config": {"workload": "stable sort, %s, n=%d, keys %s seed %d, values = index"
-                               % (args.op, n, args.dist, args.seed),
+        "config": {"workload": "stable sort, %s, n=%d, keys %s seed %d, values = index%s"
+                               % (args.op, n, args.dist, args.seed,
+                                  ", learned zones" if args.bucketing == "learned" else ""),
                    "n": n, "dist": args.dist, "l2": "inputs 8+ GB per step >> L2",
                    "parallelism": "replicas" if world > 1 else "single"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -328,8 +344,15 @@ def run_ours(args):
         "e2e": e2e,
         "stats": {"levels": stats["levels"], "phase_ms": stats["phase_ms"],
                   "heavy_keys": stats["heavy_keys"][:4],
+                  "records": stats["records"][:6],
                   "finisher_tasks": stats["finisher_tasks"],
-                  "merge_records": stats["merge_records"]},
+                  "finisher_lsd_tasks": stats["finisher_lsd_tasks"],
+                  "merge_records": stats["merge_records"],
+                  "bucketing": args.bucketing,
+                  "level0_bucket_cv": stats["learned_bucket_cv"],
+                  "level0_bucket_max_over_mean": stats["learned_bucket_max_over_mean"],
+                  "fixup_records": stats["learned_fixup_records"],
+                  "fixup_steps": stats["learned_fixup_steps"]},
         "ms_steps": ms,
     }
     if not args.no_cpu_baseline and world == 1:
@@ -441,7 +464,7 @@ def run_segmented(args):
         ms_step, ms_list = timed(step, args.steps, args.warmup)
     st = dts.dtsort_last_device_error(h, sp)
     if st != 0:
-        raise RuntimeError("device: " + dts.status_string(st))
+        raise RuntimeError("device: " + device_error_text(h, st))
     stats = dts.dtsort_get_stats(h).as_dict()
     base = None
     if args.baseline_calls:

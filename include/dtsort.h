@@ -130,13 +130,21 @@ typedef struct {
   int64_t learned_fixup_records;  /* learned bucketing: records whose predicted
                                      bucket needed the exact fix-up */
   int64_t learned_fixup_steps;
-  double learned_bucket_cv;       /* learned bucketing: coefficient of
-                                     variation of the level-0 bucket sizes */
-  double learned_bucket_max_over_mean;
+  double learned_bucket_cv;       /* coefficient of variation of the level-0
+                                     light bucket sizes (digit or learned
+                                     zones; single-array sorts) */
+  double learned_bucket_max_over_mean; /* largest / mean of the same */
   double phase_ms[8];             /* device time per phase kind: 0 setup,
                                      1 sample, 2 histogram, 3 scan, 4 scatter,
                                      5 finisher, 6 merge, 7 total */
-  int64_t reserved[8];
+  int64_t check_site;             /* first failed internal consistency check
+                                     (0: none); the call then returned
+                                     DTSORT_ERR_INTERNAL */
+  int64_t check_values[2];        /* the two values that failed it */
+  int64_t finisher_lsd_tasks;     /* base-case buckets that needed the LSD
+                                     passes (a one-pass bin held too many
+                                     equal-prefix keys) */
+  int64_t reserved[4];
 } dtsort_stats;
 
 DTSORT_API const char *dtsort_status_string(dtsort_status s);
@@ -206,6 +214,42 @@ DTSORT_API dtsort_status dtsort_last_device_error(dtsort_handle h, dtsort_stream
 
 /* Copies the statistics of the most recent sort (synchronises the device). */
 DTSORT_API dtsort_status dtsort_get_stats(dtsort_handle h, dtsort_stats *out);
+
+/* ---- learned bucketing: the model's kernels ---------------------------------
+ * The paper has no learned component.  With options.bucketing = LEARNED, a
+ * single-array sort of n >= 2^20 keys first fits a CDF model on about 1% of
+ * the keys (sampled, sorted, features x = log2(1 + key) / key_bits, targets
+ * (i + 0.5) / m), trained by Adam on the GPU; the model's inverse gives the
+ * level-0 zone boundaries, and each key's zone is predicted from the model and
+ * then fixed up exactly by integer comparison with the boundaries.  The
+ * output is the same as with digit zones.
+ *
+ * The model is a 1 -> 16 -> 16 -> 1 MLP with tanh hidden layers: 321 fp32
+ * parameters laid out W1[16] b1[16] W2[16][16] (row j, column k multiplies
+ * hidden unit k) b2[16] W3[16] b3.  These entry points run its kernels on
+ * given data (all pointers DEVICE); they need no handle.
+ *
+ * dtsort_mlp_forward: y[i] = F(x[i]).
+ * dtsort_mlp_grad:    grad_out[0..321) = gradient of (1/n) sum (F(x_i)-t_i)^2
+ *                     over the parameters, grad_out[321] = that loss
+ *                     (322 floats); partial: ceil(n/256) * 322 floats of
+ *                     scratch.  Sums run in a fixed order (deterministic).
+ * dtsort_mlp_adam:    one Adam step (beta1 0.9, beta2 0.999, eps 1e-8) at step
+ *                     number `step` >= 1 on params, moments m, v (321 each)
+ *                     with the gradient grad (322 floats as above).
+ * dtsort_mlp_train:   `steps` Adam steps on batches of `batch` points; batch
+ *                     k uses points ((k-1) mod S) + i*S, S = n / batch;
+ *                     partial: ceil(batch/256) * 322 floats. */
+DTSORT_API dtsort_status dtsort_mlp_forward(const float *params, const float *x, int64_t n,
+                                            float *y, dtsort_stream stream);
+DTSORT_API dtsort_status dtsort_mlp_grad(const float *params, const float *x, const float *t,
+                                         int64_t n, float *partial, float *grad_out,
+                                         dtsort_stream stream);
+DTSORT_API dtsort_status dtsort_mlp_adam(float *params, float *m, float *v, const float *grad,
+                                         int step, float lr, dtsort_stream stream);
+DTSORT_API dtsort_status dtsort_mlp_train(float *params, float *m, float *v, const float *x,
+                                          const float *t, int64_t n, int steps, int batch,
+                                          float lr, float *partial, dtsort_stream stream);
 
 /* ---- autotuning ------------------------------------------------------------
  * Picks the tuning knobs (digit width limit, base-case capacity, count-matrix

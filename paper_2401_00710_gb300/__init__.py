@@ -35,6 +35,7 @@ EXPORTED = [
     "dtsort_segmented_u64", "dtsort_segmented_u64_kv",
     "dtsort_last_device_error", "dtsort_get_stats", "dtsort_debug_sample",
     "dtsort_u32_kv_noalloc", "dtsort_autotune", "dtsort_autotune_scratch_bytes",
+    "dtsort_mlp_forward", "dtsort_mlp_grad", "dtsort_mlp_adam", "dtsort_mlp_train",
 ]
 
 # largest n of dtsort_u32_kv_noalloc (DTSORT_NOALLOC_MAX_N in dtsort.h)
@@ -83,7 +84,10 @@ class dtsort_stats(ctypes.Structure):
                 ("learned_bucket_cv", ctypes.c_double),
                 ("learned_bucket_max_over_mean", ctypes.c_double),
                 ("phase_ms", ctypes.c_double * 8),
-                ("reserved", ctypes.c_int64 * 8)]
+                ("check_site", ctypes.c_int64),
+                ("check_values", ctypes.c_int64 * 2),
+                ("finisher_lsd_tasks", ctypes.c_int64),
+                ("reserved", ctypes.c_int64 * 4)]
 
     def as_dict(self):
         out = {}
@@ -151,6 +155,11 @@ def _declare(L):
                                       ctypes.c_int, ctypes.c_uint64, _I64, _I64,
                                       _P, _P, _P, _P]
     L.dtsort_u32_kv_noalloc.argtypes = [_P, _P, _I64, _P, _P]
+    L.dtsort_mlp_forward.argtypes = [_P, _P, _I64, _P, _P]
+    L.dtsort_mlp_grad.argtypes = [_P, _P, _P, _I64, _P, _P, _P]
+    L.dtsort_mlp_adam.argtypes = [_P, _P, _P, _P, ctypes.c_int, ctypes.c_float, _P]
+    L.dtsort_mlp_train.argtypes = [_P, _P, _P, _P, _P, _I64, ctypes.c_int, ctypes.c_int,
+                                   ctypes.c_float, _P, _P]
     L.dtsort_autotune_scratch_bytes.argtypes = [_H, ctypes.c_int, _I64, _I64,
                                                 ctypes.POINTER(_SZ)]
     L.dtsort_autotune.argtypes = [_H, ctypes.c_int, _P, _P, _P, _I64, _I64, _P, _SZ,
@@ -262,6 +271,23 @@ def dtsort_debug_sample(h, keys, key_bytes, start, size, hi, seed, count, L,
     return lib().dtsort_debug_sample(h, keys, key_bytes, start, size, hi, seed,
                                      count, L, heavy_out, nheavy_out, max_out,
                                      stream or None)
+
+
+def dtsort_mlp_forward(params, x, n, y, stream=0):
+    return lib().dtsort_mlp_forward(params, x, n, y, stream or None)
+
+
+def dtsort_mlp_grad(params, x, t, n, partial, grad_out, stream=0):
+    return lib().dtsort_mlp_grad(params, x, t, n, partial, grad_out, stream or None)
+
+
+def dtsort_mlp_adam(params, m, v, grad, step, lr, stream=0):
+    return lib().dtsort_mlp_adam(params, m, v, grad, step, lr, stream or None)
+
+
+def dtsort_mlp_train(params, m, v, x, t, n, steps, batch, lr, partial, stream=0):
+    return lib().dtsort_mlp_train(params, m, v, x, t, n, steps, batch, lr, partial,
+                                  stream or None)
 
 
 def dtsort_autotune_scratch_bytes(h, op, n, num_segments=1):

@@ -29,6 +29,10 @@ constexpr int kOps = 4;
 struct Layout {
   size_t tkeys, tvals, ctl, segs0, segs1, info, bcount, bstart, lid, heavy, hashk, hashid,
       cmat, status, tasks, zones, mhk, mhs, mhst, total;
+  // learned bucketing (lrn_m == 0: digit zones)
+  int64_t lrn_m;
+  int lrn_B;
+  size_t lsample, lws, lws_bytes, lx, lt, lparams, lpart, lspl, ltab;
   int64_t maxseg, bmax, hmax, zmax, hashmax, cwords, swords, tmax, mhmax;
   int cap;
   int64_t target;
@@ -142,6 +146,65 @@ Layout make_layout(int kb, int vb, int64_t n, int64_t nsegs, const Opts &o,
   return L;
 }
 
+constexpr int64_t kLrnMinN = (int64_t)1 << 20;   // smaller arrays use digit zones
+constexpr int kLrnBatch = 8192;
+
+// Host copy of the device digit-width rule (plan_gamma), for the number of
+// learned zones at level 0.
+int plan_gamma_host(int64_t s, int64_t target, int gmax, int hi, int fin_dig) {
+  int e = 0;
+  while (e < 62 && (target << e) < s) ++e;
+  if (e < 1) e = 1;
+  const int nlev = (e + gmax - 1) / gmax;
+  int g = (e + nlev - 1) / nlev;
+  g = g < 1 ? 1 : (g > gmax ? gmax : g);
+  if (nlev == 1 && hi > g) {
+    int best = g, bestp = (hi - g + fin_dig - 1) / fin_dig;
+    for (int g2 = g + 1; g2 <= gmax && g2 <= hi && g2 <= g + 2; ++g2) {
+      const int p2 = (hi - g2 + fin_dig - 1) / fin_dig;
+      if (p2 < bestp) {
+        best = g2;
+        bestp = p2;
+      }
+    }
+    g = best;
+  }
+  return g;
+}
+
+// Appends the learned-bucketing region to a layout: the model sample (about
+// 1% of the keys), a workspace to sort it, features/targets, parameters and
+// Adam moments, gradient partials, zone boundaries and the prediction table.
+void add_learned(Layout &L, int kb, int64_t n, const Opts &o, const KernelShape &ks_u64) {
+  int64_t m = n / 100;
+  m = std::max<int64_t>(m, (int64_t)1 << 16);
+  m = std::min<int64_t>(m, (int64_t)1 << 24);
+  m = (m / kLrnBatch) * kLrnBatch;
+  L.lrn_m = m;
+  L.lrn_B = 1 << plan_gamma_host(n, L.target, std::min(o.gamma_max, dts::GAMMA_HW), 8 * kb,
+                                 dts::FIN_DIG);
+  Opts od = o;
+  od.cap = ks_u64.fin_cap;
+  od.blk_tiles = ks_u64.blk / ks_u64.tile;
+  const Layout S = make_layout(8, 0, m, 1, od, ks_u64);
+  size_t off = L.total;
+  auto take = [&](size_t bytes) {
+    size_t r = off;
+    off = up(off + bytes);
+    return r;
+  };
+  L.lsample = take(8 * (size_t)m);
+  L.lws_bytes = S.total;
+  L.lws = take(S.total);
+  L.lx = take(4 * (size_t)m);
+  L.lt = take(4 * (size_t)m);
+  L.lparams = take(4 * 3 * 352);
+  L.lpart = take(4 * (size_t)(kLrnBatch / 256) * 352);
+  L.lspl = take((size_t)kb * 1024);
+  L.ltab = take(4 * 1024);
+  L.total = off;
+}
+
 dtsort_status from_cuda(cudaError_t e) {
   return e == cudaSuccess ? DTSORT_OK : DTSORT_ERR_CUDA;
 }
@@ -246,7 +309,8 @@ dtsort_options tuned_options(dtsort_handle h, int op, int64_t n, int64_t nsegs) 
 }
 
 dtsort_status run_sort(dtsort_handle h, int op, void *keys, void *vals, const int64_t *offsets,
-                       int64_t nsegs, int64_t n, void *ws, size_t ws_bytes, cudaStream_t s) {
+                       int64_t nsegs, int64_t n, void *ws, size_t ws_bytes, cudaStream_t s,
+                       bool allow_learned = true) {
   if (!h) return DTSORT_ERR_INVALID_ARG;
   if (n < 0 || nsegs < 0) return DTSORT_ERR_INVALID_ARG;
   if (offsets && nsegs == 0) return n == 0 ? DTSORT_OK : DTSORT_ERR_INVALID_ARG;
@@ -264,7 +328,14 @@ dtsort_status run_sort(dtsort_handle h, int op, void *keys, void *vals, const in
   if (e != cudaSuccess) return DTSORT_ERR_CUDA;
   if (ks->blocks_per_sm < 1) return DTSORT_ERR_UNSUPPORTED;
   const Opts o = effective(tuned_options(h, op, n, offsets ? nsegs : 1), *ks);
-  const Layout L = make_layout(kb, vb, n, offsets ? nsegs : 1, o, *ks);
+  Layout L = make_layout(kb, vb, n, offsets ? nsegs : 1, o, *ks);
+  const bool learned = allow_learned && h->opt.bucketing == DTSORT_BUCKETING_LEARNED &&
+                       !offsets && n >= kLrnMinN;
+  KernelShape *ks64 = nullptr;
+  if (learned) {
+    if (get_shape(h, DTSORT_OP_U64, &ks64) != cudaSuccess) return DTSORT_ERR_CUDA;
+    add_learned(L, kb, n, o, *ks64);
+  }
   if (ws_bytes < L.total) return DTSORT_ERR_WORKSPACE_TOO_SMALL;
   char *w = (char *)ws;
   Params P{};
@@ -313,6 +384,32 @@ dtsort_status run_sort(dtsort_handle h, int op, void *keys, void *vals, const in
   P.mhmax = L.mhmax;
   P.dev_status = h->d_status;
   P.stats = h->d_stats;
+  P.lrn_B = 0;
+  if (learned) {
+    // fit the CDF model on ~1% of the keys and derive the level-0 zones:
+    // sample, sort the sample (digit zones), features, Adam training,
+    // boundaries + prediction table.  All on `s`, no host synchronisation.
+    uint64_t *smp = (uint64_t *)(w + L.lsample);
+    float *x = (float *)(w + L.lx), *t = (float *)(w + L.lt);
+    float *prm = (float *)(w + L.lparams);
+    const uint64_t lseed = o.seed ^ 0x4C6561726E6564ull;
+    if ((e = dts::lrn_gather(keys, kb, n, lseed, smp, L.lrn_m, s)) != cudaSuccess)
+      return DTSORT_ERR_CUDA;
+    const dtsort_status st = run_sort(h, DTSORT_OP_U64, smp, nullptr, nullptr, 1, L.lrn_m,
+                                      w + L.lws, L.lws_bytes, s, false);
+    if (st != DTSORT_OK) return st;
+    const int steps = h->opt.learned_train_steps > 0 ? h->opt.learned_train_steps : 200;
+    if ((e = dts::lrn_features(smp, L.lrn_m, 8 * kb, x, t, s)) != cudaSuccess ||
+        (e = dts::lrn_init(prm, prm + 352, prm + 704, lseed, s)) != cudaSuccess ||
+        (e = dts::lrn_train(prm, prm + 352, prm + 704, x, t, L.lrn_m, steps, kLrnBatch, 1e-2f,
+                            (float *)(w + L.lpart), s)) != cudaSuccess ||
+        (e = dts::lrn_splitters(prm, L.lrn_B, kb, w + L.lspl, (float *)(w + L.ltab), s)) !=
+            cudaSuccess)
+      return DTSORT_ERR_CUDA;
+    P.lrn_B = L.lrn_B;
+    P.lrn_spl = w + L.lspl;
+    P.lrn_tab = (const float *)(w + L.ltab);
+  }
   e = cudaMemsetAsync(P.ctl, 0, sizeof(dts::Ctl), s);
   if (e != cudaSuccess) return DTSORT_ERR_CUDA;
   const int grid = h->nsm * std::min(ks->blocks_per_sm, 2);
@@ -443,7 +540,13 @@ dtsort_status dtsort_workspace_bytes(dtsort_handle h, dtsort_op op, int64_t n,
   if (get_shape(h, op, &ks) != cudaSuccess) return DTSORT_ERR_CUDA;
   const Opts o = effective(tuned_options(h, op, n, num_segments > 0 ? num_segments : 1), *ks);
   const int kb = key_bytes(op), vb = has_vals(op) ? kb : 0;
-  *bytes = make_layout(kb, vb, n, num_segments > 0 ? num_segments : 1, o, *ks).total;
+  Layout L = make_layout(kb, vb, n, num_segments > 0 ? num_segments : 1, o, *ks);
+  if (h->opt.bucketing == DTSORT_BUCKETING_LEARNED && n >= kLrnMinN) {
+    KernelShape *ks64 = nullptr;
+    if (get_shape(h, DTSORT_OP_U64, &ks64) != cudaSuccess) return DTSORT_ERR_CUDA;
+    add_learned(L, kb, n, o, *ks64);
+  }
+  *bytes = L.total;
   return DTSORT_OK;
 }
 
@@ -525,6 +628,10 @@ dtsort_status dtsort_get_stats(dtsort_handle h, dtsort_stats *out) {
   out->learned_bucket_cv = d.learned_cv;
   out->learned_bucket_max_over_mean = d.learned_mom;
   for (int k = 0; k < 8; ++k) out->phase_ms[k] = d.phase_ms[k];
+  out->finisher_lsd_tasks = d.fin_lsd_tasks;
+  out->check_site = d.check_site;
+  out->check_values[0] = d.check_values[0];
+  out->check_values[1] = d.check_values[1];
   return DTSORT_OK;
 }
 

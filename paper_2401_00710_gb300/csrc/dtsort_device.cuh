@@ -25,8 +25,10 @@ namespace dts {
 constexpr int NT = 512;                       // threads per CTA, every phase
 constexpr int NWARP = NT / 32;
 constexpr int GAMMA_HW = 9;                   // widest digit of one level
-constexpr int NB_HW = (1 << GAMMA_HW) + (1 << (GAMMA_HW - 1)) + 1;  // 769
-constexpr int NB_PAD = 776;                   // NB_HW + dummy bucket, padded
+constexpr int HEAVY_HW = 128;                 // heavy keys kept per subproblem
+constexpr int NB_HW = (1 << GAMMA_HW) + HEAVY_HW + 1;  // 641
+constexpr int NB_PAD = 648;                   // NB_HW + dummy bucket, padded
+constexpr int LRN_TAB_N = 512;                // learned prediction table cells
 constexpr int SMAX = 8192;                    // largest on-chip sample
 constexpr int HASH_HW = 1 << GAMMA_HW;        // hash slots for <= 256 heavy keys
 constexpr int MAXLEV = 136;                   // > 2 * 64 + slack
@@ -41,11 +43,15 @@ enum { TASK_SORT = 0, TASK_COPY = 1 };
 enum { PH_SETUP = 0, PH_SAMPLE, PH_HIST, PH_SCAN, PH_SCATTER, PH_FINISH, PH_MERGE,
        PH_TOTAL };
 
-// A subproblem: keys in [start, start+size) agree on every bit >= hi.
+// A subproblem: records [start, start+size) whose keys all lie in
+// [base, base + 2^hi); its digits are taken from key - base.  (Below a digit
+// zone base only fixes the shared high bits; below a learned zone it is the
+// zone's lower boundary.)
 struct Seg {
   int64_t start, size;
   int64_t ntotal;   // length of the array it came from (n of Alg. 2)
-  int32_t hi;       // low bits still unsorted
+  uint64_t base;    // lower bound of the keys
+  int32_t hi;       // bits of key - base still unsorted
   uint8_t res;      // buffer (0 = caller's, 1 = workspace) the result goes to
   uint8_t pad[3];
 };
@@ -68,10 +74,13 @@ struct SegInfo {
   int64_t coff;     // count matrix, u32, nblk x nb (becomes block offsets)
   int64_t soff;     // chunk look-back status words, nchk x nb
   int64_t mhoff;    // persistent heavy store reservation (for merges)
+  int32_t learned;  // zones are the learned boundaries (level 0 only)
+  int32_t pad_;
 };
 
 struct Task {
   int64_t start, size;
+  uint64_t base;    // the records' keys lie in [base, base + 2^hi)
   int32_t hi;
   uint8_t src, dst, kind, pad;
 };
@@ -101,8 +110,14 @@ struct Ctl {
   unsigned long long lvl_chunk[MAXLEV + 1];
   long long st_segments[16], st_records[16], st_heavy_keys[16],
       st_heavy_records[16], st_overflow[16];
+  long long st_fin_lsd_tasks;
   long long st_fin_tasks, st_fin_records, st_copy_records, st_merge_zones,
-      st_merge_records;
+      st_merge_records, st_fix_records, st_fix_steps;
+  // first failed self-check: site, level, and two values
+  long long dbg[4];
+  // level-0 light bucket sizes of the first subproblem (imbalance statistics)
+  double st_bsum, st_bsq;
+  long long st_bmax, st_bnz;
   unsigned long long t_phase[8];
   unsigned long long t_last;
 };
@@ -116,7 +131,8 @@ struct DevStats {
       merge_records, learned_fixup_records, learned_fixup_steps;
   double learned_cv, learned_mom;
   double phase_ms[8];
-  int64_t reserved[8];
+  int64_t check_site, check_values[2];
+  int64_t fin_lsd_tasks;
 };
 
 struct Params {
@@ -134,7 +150,9 @@ struct Params {
   int32_t sample_factor;  // samples = 2^gamma * L * factor (capped)
   int32_t debug_fault;    // 1: chunk 1 of level 0 never publishes (tests)
   int32_t blk_tiles;      // tiles per count-matrix row (block = blk_tiles * TILE)
-  int32_t pad1;
+  int32_t lrn_B;          // learned zones at level 0 (0: digit zones)
+  const void *lrn_spl;    // lrn_B zone lower bounds (key type), spl[0] = 0
+  const float *lrn_tab;   // LRN_TAB_N + 1 predicted CDF values on the feature grid
   unsigned long long wait_ns;  // bound of every spin-wait
   Ctl *ctl;
   Seg *segs[2];
@@ -199,6 +217,15 @@ __device__ __forceinline__ long long atomic_add_ll(long long *p, long long v) {
 __device__ __forceinline__ void latch(const Params &P, int code) {
   atomicCAS(&P.ctl->error, 0, code);
   atomicCAS(P.dev_status, 0, code);
+}
+
+// A failed self-check: latch ERR_INTERNAL and record where (first one wins).
+static __device__ __noinline__ void check_failed(const Params &P, int site, long long a, long long b) {
+  if (atomicCAS((unsigned long long *)&P.ctl->dbg[0], 0ull, (unsigned long long)site) == 0ull) {
+    P.ctl->dbg[1] = a;
+    P.ctl->dbg[2] = b;
+  }
+  latch(P, ERR_INTERNAL);
 }
 
 __device__ __forceinline__ uint64_t sm64_fmix(uint64_t z) {
@@ -285,51 +312,47 @@ __device__ __forceinline__ T block_excl_scan(T v, T *sh, T &total) {
   return base + x - v;
 }
 
-// Rank of this lane's item among the warp's items with the same bucket that
-// come earlier in (round, lane) order; wc is the warp's counter row.  The
-// lanes holding the same bucket are found with one ballot per bit of the
-// bucket id (nbits bits), whose cost does not grow with the number of
-// distinct buckets in the warp.
+// Digit of a key on the fast path: bits [lo, lo + log2(gmask+1)) of
+// key - base (32-bit arithmetic for 32-bit keys).
+template <typename K>
+__device__ __forceinline__ unsigned fast_digit(K key, uint64_t base, int lo, unsigned gmask) {
+  if constexpr (sizeof(K) == 4) return (((uint32_t)key - (uint32_t)base) >> lo) & gmask;
+  else return (unsigned)(((uint64_t)key - base) >> lo) & gmask;
+}
+
+// Minimum / maximum over the warp (all lanes active).
+template <typename T>
+__device__ __forceinline__ T warp_min(T v) {
+  if constexpr (sizeof(T) == 4) {
+    return (T)__reduce_min_sync(0xffffffffu, (unsigned)v);
+  } else {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const T u = __shfl_xor_sync(0xffffffffu, v, o);
+      v = u < v ? u : v;
+    }
+    return v;
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_max(T v) {
+  if constexpr (sizeof(T) == 4) {
+    return (T)__reduce_max_sync(0xffffffffu, (unsigned)v);
+  } else {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const T u = __shfl_xor_sync(0xffffffffu, v, o);
+      v = u > v ? u : v;
+    }
+    return v;
+  }
+}
+
 __device__ __forceinline__ unsigned lanemask_lt() {
   unsigned m;
   asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
   return m;
-}
-
-__device__ __forceinline__ unsigned warp_peers(unsigned b, int nbits) {
-  unsigned peers = 0xffffffffu;
-  for (int k = 0; k < nbits; ++k) {
-    const unsigned bit = (b >> k) & 1u;
-    const unsigned bal = __ballot_sync(0xffffffffu, bit);
-    peers &= bit ? bal : ~bal;
-  }
-  return peers;
-}
-
-template <int NBITS>
-__device__ __forceinline__ unsigned warp_peers_fixed(unsigned b) {
-  unsigned peers = 0xffffffffu;
-#pragma unroll
-  for (int k = 0; k < NBITS; ++k) {
-    const unsigned bit = (b >> k) & 1u;
-    const unsigned bal = __ballot_sync(0xffffffffu, bit);
-    peers &= bit ? bal : ~bal;
-  }
-  return peers;
-}
-
-__device__ __forceinline__ unsigned warp_rank_peers(unsigned b, unsigned peers, uint16_t *wc) {
-  const unsigned lane = threadIdx.x & 31;
-  const unsigned leader = __ffs(peers) - 1;
-  const unsigned before = __popc(peers & lanemask_lt());
-  unsigned old = 0;
-  if (lane == leader) {
-    old = wc[b];
-    wc[b] = (uint16_t)(old + __popc(peers));
-  }
-  old = __shfl_sync(0xffffffffu, old, leader);
-  __syncwarp();
-  return old + before;
 }
 
 // Stable rank among this warp's earlier items (in (round, lane) order) with
@@ -396,16 +419,60 @@ template <typename K>
 struct SegTables {
   SegInfo info;
   int64_t start, size;
+  uint64_t base;
   int32_t hi, seg;
   uint8_t res;
 };
 
+// Learned zone of a key: the model's distilled CDF (table on the feature
+// grid, linear between cells) predicts a zone, which is then moved to the
+// exact zone z with spl[z] <= key < spl[z+1] by integer comparisons.
+// *steps receives how far the prediction was off.
+template <typename K>
+__device__ __forceinline__ unsigned learned_zone(K key, const K *spl, const float *tab, int B,
+                                                 unsigned *steps) {
+  const float x = log2f((float)key + 1.0f) * (1.0f / (8.0f * sizeof(K)));
+  float fc = x * (float)LRN_TAB_N;
+  int c = (int)fc;
+  c = c < 0 ? 0 : (c > LRN_TAB_N - 1 ? LRN_TAB_N - 1 : c);
+  const float fr = fc - (float)c;
+  const float pz = fmaf(fr, tab[c + 1] - tab[c], tab[c]) * (float)B;
+  int z = (int)pz;
+  z = z < 0 ? 0 : (z > B - 1 ? B - 1 : z);
+  unsigned st = 0;
+  while (z > 0 && key < spl[z]) {
+    --z;
+    ++st;
+  }
+  while (z < B - 1 && key >= spl[z + 1]) {
+    ++z;
+    ++st;
+  }
+  *steps = st;
+  return (unsigned)z;
+}
+
+// Exact learned zone by binary search over the boundaries (global memory).
+template <typename K>
+__device__ __forceinline__ unsigned learned_zone_exact(K key, const K *spl, int B) {
+  int lo = 0, hi = B - 1;  // largest z with spl[z] <= key
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (ld_key<K>(spl + mid) <= key) lo = mid;
+    else hi = mid - 1;
+  }
+  return (unsigned)lo;
+}
+
 // GetBucketId (Alg. 2): heavy keys through H, overflow past the sampled key
-// range, light keys through L by their MSD zone.  lid/hk/hid: the tables in
-// shared memory.
+// range, light keys through L by their MSD zone (or learned zone).
+// lid/hk/hid/spl/tab: the tables in shared memory.
 template <typename K>
 __device__ __forceinline__ unsigned bucket_of(const SegTables<K> &T, const int32_t *lid,
-                                              const K *hk, const uint16_t *hid, K key) {
+                                              const K *hk, const uint16_t *hid, K key,
+                                              const K *spl = nullptr,
+                                              const float *tab = nullptr,
+                                              unsigned *steps = nullptr) {
   const SegInfo &I = T.info;
   if (I.hbits) {
     const uint32_t cap1 = (1u << I.hbits) - 1u;
@@ -417,27 +484,55 @@ __device__ __forceinline__ unsigned bucket_of(const SegTables<K> &T, const int32
       s = (s + 1) & cap1;
     }
   }
-  const uint64_t m = (uint64_t)key & lowmask(T.hi);
+  if (I.learned) {
+    unsigned st;
+    const unsigned z = learned_zone<K>(key, spl, tab, 1 << I.gamma, &st);
+    if (steps) *steps = st;
+    return (unsigned)lid[z];
+  }
+  const uint64_t m = ((uint64_t)key - T.base) & lowmask(T.hi);
   if (I.t < 64 && (m >> I.t) != 0) return (unsigned)(I.nb - 1);
   return (unsigned)lid[m >> I.lo];
 }
 
 template <typename K>
 __device__ __forceinline__ void load_tables(const Params &P, int seg, int level, SegTables<K> &T,
-                                            int32_t *lid_s, K *hk_s, uint16_t *hid_s) {
+                                            int32_t *lid_s, K *hk_s, uint16_t *hid_s,
+                                            K *spl_s = nullptr, float *tab_s = nullptr) {
   // all threads call; T lives in shared memory
   if (threadIdx.x == 0) {
     const Seg S = ldcg_obj(&P.segs[level & 1][seg]);
     T.info = ldcg_obj(&P.info[seg]);
     T.start = S.start;
     T.size = S.size;
+    T.base = S.base;
     T.hi = S.hi;
     T.res = S.res;
     T.seg = seg;
+    // self-check of the subproblem's tables; a bad one is recorded and
+    // turned into an empty subproblem so that nothing is indexed with it
+    const SegInfo &I = T.info;
+    const int zb = I.learned ? I.gamma : I.t - I.lo;
+    if (S.start < 0 || S.size < 0 || S.start + S.size > P.n || zb < 0 || zb > GAMMA_HW ||
+        I.nb < 1 || I.nb > NB_HW || I.hbits < 0 || I.hbits > GAMMA_HW ||
+        (I.learned && P.lrn_B > (1 << GAMMA_HW))) {
+      check_failed(P, 5, seg, (long long)I.nb * 65536 + zb * 256 + I.hbits);
+      T.size = 0;
+      T.info.nb = 0;
+      T.info.t = T.info.lo = 0;
+      T.info.hbits = 0;
+      T.info.learned = 0;
+      T.info.zoff = 0;
+    }
   }
   __syncthreads();
-  const int nz = (1 << (T.info.t - T.info.lo)) + 1;
+  const int nz = (T.info.learned ? (1 << T.info.gamma) : (1 << (T.info.t - T.info.lo))) + 1;
   for (int i = threadIdx.x; i < nz; i += NT) lid_s[i] = __ldcg(P.lid + T.info.zoff + i);
+  if (T.info.learned && spl_s) {
+    const K *spl = (const K *)P.lrn_spl;
+    for (int i = threadIdx.x; i < P.lrn_B; i += NT) spl_s[i] = ld_key<K>(spl + i);
+    for (int i = threadIdx.x; i <= LRN_TAB_N; i += NT) tab_s[i] = __ldcg(P.lrn_tab + i);
+  }
   if (T.info.hbits) {
     const int cap = 1 << T.info.hbits;
     const K *hk = (const K *)P.hash_keys + T.info.hashoff;

@@ -16,6 +16,16 @@ struct Shape {
                                       ? (96 * 1024) / (2 * (KB + VB)) : 6144;
   static constexpr int FIN_BYTES = 2 * FIN_CAP * (KB + VB);  // base-case buffers
   static constexpr int FIN_IT = FIN_CAP / NT;           // base-case items / thread
+  // one-pass base case: up to 2^FIN_FB bins over the task's key range, plus
+  // (with values) the records' original indices, in the first record buffer
+  // (each thread's run of bins is followed by one pad word, so that the
+  // lanes of a warp walking their runs hit distinct banks)
+  static constexpr int FIN_FB =
+      4 * (8192 + NT) + (HV ? 2 * FIN_CAP : 0) <= FIN_CAP * (KB + VB) ? 13 : 12;
+  static constexpr int FIN_NBIN = 1 << FIN_FB;
+  static constexpr int FIN_PER = FIN_NBIN / NT;         // most bins per thread
+  static constexpr int FIN_NBW = FIN_NBIN + NT;         // words of the padded bins
+  static constexpr int FIN_CMAX = 16;                   // largest bin sorted in place
   static constexpr int STAGE = TILE * KB;               // scatter staging (keys or values)
   static constexpr int BLK_TILES = 4;                   // tiles per count-matrix row
   static constexpr int BLK = BLK_TILES * TILE;          // records per block
@@ -65,6 +75,7 @@ constexpr size_t smem_bytes() {
   const size_t slot_b = 4 * (size_t)NWARP * NB_PAD;
   sc += 16 + (slot_b > stage_b ? slot_b : stage_b);  // rank slots / staged tile
   sc += 16 + 8 * (NWARP + 1) + 256;
+  sc += 16 + sizeof(K) * (1 << GAMMA_HW) + 16 + 4 * (LRN_TAB_N + 1);  // learned tables
   // base case
   size_t fin = 0;
   fin += 16 + (size_t)S::FIN_BYTES;
@@ -95,6 +106,7 @@ __device__ __forceinline__ void push_copy(const Params &P, int64_t start, int64_
     Task t;
     t.start = start + a;
     t.size = size - a < COPY_CHUNK ? size - a : COPY_CHUNK;
+    t.base = 0;
     t.hi = 0;
     t.src = (uint8_t)src;
     t.dst = (uint8_t)dst;
@@ -114,8 +126,8 @@ __device__ __forceinline__ void push_seg(const Params &P, int list, const Seg &s
 
 // A bucket that still needs work: recurse, sort on chip, or just move it.
 __device__ __forceinline__ void emit_child(const Params &P, int next_list, int64_t start,
-                                           int64_t size, int hi, int data_buf, int res_buf,
-                                           int64_t ntotal) {
+                                           int64_t size, int hi, uint64_t base, int data_buf,
+                                           int res_buf, int64_t ntotal) {
   if (size <= 0) return;
   if (hi == 0 || size == 1) {
     push_copy(P, start, size, data_buf, res_buf);
@@ -123,6 +135,7 @@ __device__ __forceinline__ void emit_child(const Params &P, int next_list, int64
     Task t;
     t.start = start;
     t.size = size;
+    t.base = base;
     t.hi = hi;
     t.src = (uint8_t)data_buf;
     t.dst = (uint8_t)res_buf;
@@ -133,6 +146,7 @@ __device__ __forceinline__ void emit_child(const Params &P, int next_list, int64
     s.start = start;
     s.size = size;
     s.ntotal = ntotal;
+    s.base = base;
     s.hi = hi;
     s.res = (uint8_t)res_buf;
     push_seg(P, next_list, s);
@@ -155,7 +169,7 @@ __device__ void phase_seed(const Params &P) {
         continue;
       }
     }
-    emit_child(P, 0, a, b - a, P.key_bits, 0, 0, b - a);
+    emit_child(P, 0, a, b - a, P.key_bits, 0, 0, 0, b - a);
   }
 }
 
@@ -177,11 +191,12 @@ __device__ void phase_setup(const Params &P, int level, unsigned char *smem) {
       const Seg s = ldcg_obj(&P.segs[p][i]);
       sz = s.size;
       g = plan_gamma(s.size, P.target, P.gamma_max, s.hi, FIN_DIG);
+      if (level == 0 && P.lrn_B > 0) g = 31 - __clz(P.lrn_B);  // learned zones
       const int64_t blk = (int64_t)P.blk_tiles * S::TILE;
       nblk = (s.size + blk - 1) / blk;
       nchk = (nblk + S::CH - 1) / S::CH;
-      nbm = (1 << g) + (1 << (g - 1)) + 1;
-      hm = 1 << (g - 1);
+      hm = (1 << (g - 1)) < HEAVY_HW ? (1 << (g - 1)) : HEAVY_HW;
+      nbm = (1 << g) + hm + 1;
       zm = (1 << g) + 1;
       hsm = 1 << g;
       cm = nblk * nbm;
@@ -215,6 +230,8 @@ __device__ void phase_setup(const Params &P, int level, unsigned char *smem) {
       I.coff = o_c;
       I.soff = o_s;
       I.mhoff = 0;
+      I.learned = 0;
+      I.pad_ = 0;
       P.info[i] = I;
     }
   }
@@ -257,7 +274,9 @@ __device__ void phase_sample(const Params &P, int level, unsigned char *smem) {
     const Seg S = ldcg_obj(&P.segs[p][si]);
     SegInfo I = ldcg_obj(&P.info[si]);
     const int g = I.gamma;
-    const int64_t nbm = (1 << g) + (1 << (g - 1)) + 1;
+    const int hcap = (1 << (g - 1)) < HEAVY_HW ? (1 << (g - 1)) : HEAVY_HW;
+    const int64_t nbm = (1 << g) + hcap + 1;
+    const bool learned = level == 0 && P.lrn_B > 0;
     for (int64_t b = threadIdx.x; b < nbm; b += NT) P.bcount[I.boff + b] = 0;
     int L = 0;
     while (L < 63 && (1ll << L) < S.ntotal) ++L;
@@ -295,10 +314,16 @@ __device__ void phase_sample(const Params &P, int level, unsigned char *smem) {
       }
     }
     // key range from the largest sample (overflow bucket above it)
-    const uint64_t rmax = (uint64_t)Ssm[m - 1] & lowmask(S.hi);
-    const int t = bitlen64(rmax);
-    const int lo = t - g > 0 ? t - g : 0;
-    const int geff = t - lo;
+    const uint64_t rmax = ((uint64_t)Ssm[m - 1] - S.base) & lowmask(S.hi);
+    // learned zones cover the whole key range: no overflow bucket is used
+    const int t = learned ? S.hi : bitlen64(rmax);
+    const int lo = learned ? 0 : (t - g > 0 ? t - g : 0);
+    const int geff = learned ? g : t - lo;
+    const K *lspl = (const K *)P.lrn_spl;
+    auto zone_of = [&](K key) -> uint64_t {
+      return learned ? (uint64_t)learned_zone_exact<K>(key, lspl, 1 << g)
+                     : ((((uint64_t)key - S.base) & lowmask(S.hi)) >> lo);
+    };
     // heavy keys: seen at least twice among S[L-1], S[2L-1], ...
     int nh = 0;
     if (P.heavy_on) {
@@ -319,7 +344,6 @@ __device__ void phase_sample(const Params &P, int level, unsigned char *smem) {
         carry += tot;
       }
       nh = (int)carry;
-      const int hcap = 1 << (g - 1);
       if (nh > hcap) nh = hcap;
       if (nh > 0) {
         // room for this subproblem's heavy buckets in the merge store
@@ -341,7 +365,7 @@ __device__ void phase_sample(const Params &P, int level, unsigned char *smem) {
       int a = 0, b = nh;
       while (a < b) {
         const int mid = (a + b) >> 1;
-        const uint64_t zm = ((uint64_t)hv[mid] & lowmask(S.hi)) >> lo;
+        const uint64_t zm = zone_of(hv[mid]);
         if (zm < (uint64_t)z) a = mid + 1;
         else b = mid;
       }
@@ -357,7 +381,7 @@ __device__ void phase_sample(const Params &P, int level, unsigned char *smem) {
       if (threadIdx.x == 0) {
         for (int j = 0; j < nh; ++j) {
           const K key = hv[j];
-          const int zone = (int)(((uint64_t)key & lowmask(S.hi)) >> lo);
+          const int zone = (int)zone_of(key);
           uint32_t s = hash_slot<K>(key, hbits);
           while (hid[s] != HEMPTY) s = (s + 1) & (uint32_t)(cap - 1);
           hk[s] = key;
@@ -377,6 +401,7 @@ __device__ void phase_sample(const Params &P, int level, unsigned char *smem) {
       I.nheavy = nh;
       I.nb = nz + nh + 1;
       I.hbits = hbits;
+      I.learned = learned ? 1 : 0;
       P.info[si] = I;
       atomic_add_ll(&c->st_heavy_keys[level < 15 ? level : 15], (long long)nh);
     }
@@ -401,21 +426,31 @@ __device__ void phase_hist(const Params &P, int level, unsigned char *smem) {
   K *hk_s = cv.take<K>(HASH_HW);
   uint16_t *hid_s = cv.take<uint16_t>(HASH_HW);
   unsigned *cnt = cv.take<unsigned>(NB_PAD);
+  K *spl_s = cv.take<K>(1 << GAMMA_HW);
+  float *tab_s = cv.take<float>(LRN_TAB_N + 1);
+  long long fix_recs = 0, fix_steps = 0;
+  unsigned bad = 0;  // a bucket id out of range (self-check), reported once
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int64_t r0 = nblocks * blockIdx.x / gridDim.x;
   const int64_t r1 = nblocks * (blockIdx.x + 1) / gridDim.x;
+  // the current subproblem and the end of its blocks, in registers: T is
+  // rewritten by thread 0 when the next one is loaded
   int cur = -1;
+  int64_t cur_end = 0;
   for (int64_t r = r0; r < r1; ++r) {
-    int s = cur;
-    if (cur < 0 || r >= T.info.blk0 + T.info.nblk) s = find_blk_seg(P, nseg, r);
-    if (s != cur) {
-      load_tables<K>(P, s, level, T, lid_s, hk_s, hid_s);
-      cur = s;
+    if (cur < 0 || r >= cur_end) {
+      const int s = find_blk_seg(P, nseg, r);
+      if (s != cur) {
+        load_tables<K>(P, s, level, T, lid_s, hk_s, hid_s, spl_s, tab_s);
+        cur = s;
+      }
+      cur_end = T.info.blk0 + T.info.nblk;
     }
     const int nb = T.info.nb;
     const int lo = T.info.lo;
     const unsigned gmask = (1u << (T.info.t - T.info.lo)) - 1u;
-    const bool fast = T.info.hbits == 0 && T.info.t >= T.hi;
+    const bool fast = T.info.hbits == 0 && T.info.t >= T.hi && !T.info.learned;
+    const uint64_t kbase = T.base;
     const int64_t lr = r - T.info.blk0;
     if (lr % S::CH == 0) {  // this chunk's look-back status starts empty
       const int64_t row = T.info.soff + (lr / S::CH) * nb;
@@ -440,13 +475,21 @@ __device__ void phase_hist(const Params &P, int level, unsigned char *smem) {
 #pragma unroll
         for (int j = 0; j < S::ITEMS; ++j) {
           const int i = w * 32 * S::ITEMS + j * 32 + lane;
-          if (i < tn) atomicAdd(&cnt[(unsigned)((uint64_t)key[j] >> lo) & gmask], 1u);
+          // b <= gmask < nb: the tables were checked when loaded
+          if (i < tn) atomicAdd(&cnt[fast_digit<K>(key[j], kbase, lo, gmask)], 1u);
         }
       } else {
 #pragma unroll
         for (int j = 0; j < S::ITEMS; ++j) {
           const int i = w * 32 * S::ITEMS + j * 32 + lane;
-          if (i < tn) atomicAdd(&cnt[bucket_of<K>(T, lid_s, hk_s, hid_s, key[j])], 1u);
+          if (i < tn) {
+            unsigned st = 0;
+            const unsigned b = bucket_of<K>(T, lid_s, hk_s, hid_s, key[j], spl_s, tab_s, &st);
+            if (b < (unsigned)nb) atomicAdd(&cnt[b], 1u);
+            else bad = b;
+            fix_recs += st != 0;
+            fix_steps += st;
+          }
         }
       }
     }
@@ -455,6 +498,11 @@ __device__ void phase_hist(const Params &P, int level, unsigned char *smem) {
     for (int b = threadIdx.x; b < nb; b += NT) row[b] = cnt[b];
     __syncthreads();
   }
+  if (fix_recs) {
+    atomic_add_ll(&c->st_fix_records, fix_recs);
+    atomic_add_ll(&c->st_fix_steps, fix_steps);
+  }
+  if (bad) check_failed(P, 3, bad, level);
 }
 
 // ------------------------------------------------- count-matrix scan
@@ -559,7 +607,7 @@ __device__ void phase_scan(const Params &P, int level, unsigned char *smem) {
     if (i0 < NB_PAD) excl[i0] = o;
     if (i1 < NB_PAD) excl[i1] = o + v0;
     if (threadIdx.x == 0) excl[NB_PAD] = tot;
-    const int nz = 1 << (I.t - I.lo);
+    const int nz = I.learned ? (1 << I.gamma) : (1 << (I.t - I.lo));
     for (int z = threadIdx.x; z <= nz; z += NT) lid_s[z] = __ldcg(P.lid + I.zoff + z);
     __syncthreads();
     for (int b = threadIdx.x; b < nb; b += NT) P.bstart[I.boff + b] = S.start + excl[b];
@@ -567,6 +615,10 @@ __device__ void phase_scan(const Params &P, int level, unsigned char *smem) {
     long long heavy_recs = 0;
     for (int z = threadIdx.x; z < nz; z += NT) {
       const int lb = lid_s[z], le = lid_s[z + 1];
+      if (lb < 0 || le <= lb || le > nb - 1) {
+        check_failed(P, 7, z, (long long)lb * 65536 + le);
+        continue;
+      }
       const int m = le - lb - 1;
       const int64_t zs = S.start + excl[lb];
       const int64_t b0 = cntv[lb];
@@ -597,13 +649,31 @@ __device__ void phase_scan(const Params &P, int level, unsigned char *smem) {
         // heavy runs must sit in the merge's input buffer
         if (dstb == res) push_copy(P, zs + b0, ze - zs - b0, dstb, dstb ^ 1);
       }
-      emit_child(P, p ^ 1, zs, b0, I.lo, dstb, light_res, S.ntotal);
+      // the light bucket's keys: digit zone z covers base + [z, z+1) * 2^lo;
+      // learned zone z covers [spl[z], spl[z+1])
+      int chi = I.lo;
+      uint64_t cbase = S.base + ((uint64_t)z << I.lo);
+      if (I.learned) {
+        const K *spl = (const K *)P.lrn_spl;
+        const uint64_t a = (uint64_t)ld_key<K>(spl + z);
+        const uint64_t top = z + 1 < nz ? (uint64_t)ld_key<K>(spl + z + 1) - 1
+                                        : (uint64_t)(K)~(K)0;
+        cbase = a;
+        chi = top >= a ? bitlen64(top - a) : 0;
+      }
+      emit_child(P, p ^ 1, zs, b0, chi, cbase, dstb, light_res, S.ntotal);
+      if (level == 0 && si == 0) {
+        atomicAdd(&c->st_bsum, (double)b0);
+        atomicAdd(&c->st_bsq, (double)b0 * (double)b0);
+        atomicMax((unsigned long long *)&c->st_bmax, (unsigned long long)b0);
+      }
     }
+    if (level == 0 && si == 0 && threadIdx.x == 0) c->st_bnz = nz;
     if (threadIdx.x == 0) {
       const int ob = nb - 1;
       const int64_t os = S.start + excl[ob], ol = cntv[ob];
       if (ol > 0) {
-        emit_child(P, p ^ 1, os, ol, S.hi, dstb, res, S.ntotal);
+        emit_child(P, p ^ 1, os, ol, S.hi, S.base, dstb, res, S.ntotal);
         atomic_add_ll(&c->st_overflow[level < 15 ? level : 15], (long long)ol);
       }
     }
@@ -640,6 +710,8 @@ __device__ void phase_scatter(const Params &P, int level, unsigned char *smem) {
   unsigned *gbase = cv.take<unsigned>(NB_PAD);
   unsigned *base = cv.take<unsigned>(NB_PAD);
   unsigned *sh = cv.take<unsigned>(NWARP + 1);
+  K *spl_s = cv.take<K>(1 << GAMMA_HW);
+  float *tab_s = cv.take<float>(LRN_TAB_N + 1);
   // ranking slots and the staged tile share one area (never live together)
   constexpr int AREA = (4 * NWARP * NB_PAD > S::TILE * (int)sizeof(K) + 4 * S::TILE)
                            ? 4 * NWARP * NB_PAD : S::TILE * (int)sizeof(K) + 4 * S::TILE;
@@ -648,22 +720,29 @@ __device__ void phase_scatter(const Params &P, int level, unsigned char *smem) {
   K *stage = (K *)area;
   unsigned *dest = (unsigned *)(area + S::TILE * sizeof(K));  // offset in the subproblem
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  unsigned bad = 0;  // self-check: a slot or destination out of range, reported once
   uint16_t *mywc = wcnt + w * NB_PAD;
   unsigned *myslot = slots + w * NB_PAD;
   const int64_t r0 = nblocks * blockIdx.x / gridDim.x;
   const int64_t r1 = nblocks * (blockIdx.x + 1) / gridDim.x;
+  // the current subproblem and the end of its blocks, in registers: T is
+  // rewritten by thread 0 when the next one is loaded
   int cur = -1;
+  int64_t cur_end = 0;
   for (int64_t r = r0; r < r1; ++r) {
-    int s = cur;
-    if (cur < 0 || r >= T.info.blk0 + T.info.nblk) s = find_blk_seg(P, nseg, r);
-    if (s != cur) {
-      load_tables<K>(P, s, level, T, lid_s, hk_s, hid_s);
-      cur = s;
+    if (cur < 0 || r >= cur_end) {
+      const int s = find_blk_seg(P, nseg, r);
+      if (s != cur) {
+        load_tables<K>(P, s, level, T, lid_s, hk_s, hid_s, spl_s, tab_s);
+        cur = s;
+      }
+      cur_end = T.info.blk0 + T.info.nblk;
     }
     const int nb = T.info.nb;
     const int lo = T.info.lo;
     const unsigned gmask = (1u << (T.info.t - T.info.lo)) - 1u;
-    const bool fast = T.info.hbits == 0 && T.info.t >= T.hi;
+    const bool fast = T.info.hbits == 0 && T.info.t >= T.hi && !T.info.learned;
+    const uint64_t kbase = T.base;
     const int64_t lr = r - T.info.blk0;
     const unsigned *X = P.cmat + T.info.coff + lr * nb;
     for (int b = threadIdx.x; b < nb; b += NT)
@@ -697,14 +776,15 @@ __device__ void phase_scatter(const Params &P, int level, unsigned char *smem) {
 #pragma unroll
         for (int j = 0; j < S::ITEMS; ++j) {
           const int i = w * 32 * S::ITEMS + j * 32 + lane;
-          const unsigned b = i < tn ? ((unsigned)((uint64_t)key[j] >> lo) & gmask) : (unsigned)nb;
+          const unsigned b = i < tn ? fast_digit<K>(key[j], kbase, lo, gmask) : (unsigned)nb;
           br[j] = (b << 16) | warp_rank_slots(b, myslot, mywc);
         }
       } else {
 #pragma unroll
         for (int j = 0; j < S::ITEMS; ++j) {
           const int i = w * 32 * S::ITEMS + j * 32 + lane;
-          const unsigned b = i < tn ? bucket_of<K>(T, lid_s, hk_s, hid_s, key[j]) : (unsigned)nb;
+          const unsigned b =
+              i < tn ? bucket_of<K>(T, lid_s, hk_s, hid_s, key[j], spl_s, tab_s) : (unsigned)nb;
           br[j] = (b << 16) | warp_rank_slots(b, myslot, mywc);
         }
       }
@@ -743,6 +823,11 @@ __device__ void phase_scatter(const Params &P, int level, unsigned char *smem) {
         if (i < tn) {
           const unsigned b = br[j] >> 16;
           const unsigned pj = toff[b] + wcnt[w * NB_PAD + b] + (br[j] & 0xFFFFu);
+          if (b >= (unsigned)nb || pj >= (unsigned)tn) {
+            bad = 1u + pj;
+            br[j] = 0;
+            continue;
+          }
           stage[pj] = key[j];
           dest[pj] = gbase[b] + pj;
           br[j] = pj;
@@ -761,7 +846,7 @@ __device__ void phase_scatter(const Params &P, int level, unsigned char *smem) {
       for (int q = threadIdx.x; q < tn; q += NT) {
         const unsigned d = dest[q];
         if (d < seg_size) dseg[d] = stage[q];
-        else latch(P, ERR_INTERNAL);
+        else bad = 1u + d;
       }
       if constexpr (HV) {
         __syncthreads();
@@ -779,6 +864,7 @@ __device__ void phase_scatter(const Params &P, int level, unsigned char *smem) {
       __syncthreads();
     }
   }
+  if (bad) check_failed(P, 1, bad - 1u, level);
 }
 
 // ------------------------------------------------------- base case + copy
@@ -797,17 +883,37 @@ __device__ void phase_finish(const Params &P, int level, unsigned char *smem) {
   unsigned *sh = cv.take<unsigned>(NWARP + 1);
   long long *task_sh = cv.take<long long>(1);
   int *flag_sh = cv.take<int>(1);
+  K *kmin_sh = cv.take<K>(1);
+  K *kmax_sh = cv.take<K>(1);
+  unsigned *cmax_sh = cv.take<unsigned>(1);
   static_assert(sizeof(RecT) * S::FIN_CAP >= 4 * NWARP * FIN_NB, "slots fit in a buffer");
+  static_assert(sizeof(RecT) * S::FIN_CAP >= 4 * S::FIN_NBW + (HV ? 2 * S::FIN_CAP : 0),
+                "bins and indices fit in a buffer");
+  static_assert(S::FIN_CAP < 65536, "indices fit in 16 bits");
+  static_assert(NT == 512 && S::FIN_FB >= 9, "bin runs");
+  unsigned *bins = (unsigned *)ra;                            // one-pass bins (padded)
+  uint16_t *ix = (uint16_t *)((unsigned char *)ra + 4 * S::FIN_NBW);  // original index
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   uint16_t *mywc = wcnt + w * FIN_NB;
-  long long my_recs = 0, my_tasks = 0, my_copy = 0;
+  long long my_recs = 0, my_tasks = 0, my_copy = 0, my_lsd = 0;
+  unsigned bad = 0;  // self-check: a base-case slot out of range, reported once
   while (true) {
-    if (threadIdx.x == 0) *task_sh = atomic_add_ll(&c->task_ctr, 1ll);
+    if (threadIdx.x == 0) {
+      *task_sh = atomic_add_ll(&c->task_ctr, 1ll);
+      *kmin_sh = (K)~(K)0;
+      *kmax_sh = (K)0;
+      *cmax_sh = 0u;
+    }
     __syncthreads();
     const int64_t ti = *task_sh;
     __syncthreads();
     if (ti >= ntasks) break;
     const Task tk = ldcg_obj(&P.tasks[ti]);
+    if (tk.src > 1 || tk.dst > 1 || tk.start < 0 || tk.size < 0 || tk.start + tk.size > P.n ||
+        (tk.kind != TASK_COPY && (tk.size > S::FIN_CAP || tk.hi < 0 || tk.hi > 64))) {
+      if (threadIdx.x == 0) check_failed(P, 6, ti, tk.size);
+      continue;
+    }
     const K *ksrc = (const K *)P.keys[tk.src];
     K *kdst = (K *)P.keys[tk.dst];
     const K *vsrc = HV ? (const K *)P.vals[tk.src] : nullptr;
@@ -821,28 +927,158 @@ __device__ void phase_finish(const Params &P, int level, unsigned char *smem) {
       continue;
     }
     const int n = (int)tk.size;
-    {
-      RecT rr[S::FIN_IT];
+    my_recs += n;
+    my_tasks += 1;
+    // records in registers (item j of thread t is record j * NT + t), and
+    // the task's key range
+    const int R = (n + NT - 1) / NT;  // rounds with live items (same for all threads)
+    const K *ks = ksrc + tk.start;
+    const K *vs = HV ? vsrc + tk.start : nullptr;
+    K *kd = kdst + tk.start;
+    K *vd = HV ? vdst + tk.start : nullptr;
+    RecT rr[S::FIN_IT];
+    K kmn = (K)~(K)0, kmx = (K)0;
 #pragma unroll
-      for (int j = 0; j < S::FIN_IT; ++j) {
+    for (int j = 0; j < S::FIN_IT; ++j) {
+      if (j < R) {
         const int i = j * NT + threadIdx.x;
         if (i < n) {
-          rr[j].k = ld_key<K>(ksrc + tk.start + i);
-          if constexpr (HV) rr[j].v = ld_key<K>(vsrc + tk.start + i);
+          rr[j].k = ld_key<K>(ks + i);
+          if constexpr (HV) rr[j].v = ld_key<K>(vs + i);
+          kmn = rr[j].k < kmn ? rr[j].k : kmn;
+          kmx = rr[j].k > kmx ? rr[j].k : kmx;
         }
       }
+    }
+    kmn = warp_min(kmn);
+    kmx = warp_max(kmx);
+    if (lane == 0) {
+      if constexpr (sizeof(K) == 4) {
+        atomicMin((unsigned *)kmin_sh, (unsigned)kmn);
+        atomicMax((unsigned *)kmax_sh, (unsigned)kmx);
+      } else {
+        atomicMin((unsigned long long *)kmin_sh, (unsigned long long)kmn);
+        atomicMax((unsigned long long *)kmax_sh, (unsigned long long)kmx);
+      }
+    }
+    __syncthreads();
+    const K kmin = *kmin_sh;
+    const uint64_t span = (uint64_t)(*kmax_sh) - (uint64_t)kmin;
+    if (span == 0) {  // one key: the stable order is the input order
 #pragma unroll
       for (int j = 0; j < S::FIN_IT; ++j) {
         const int i = j * NT + threadIdx.x;
-        if (i < n) ra[i] = rr[j];
+        if (j < R && i < n) {
+          kd[i] = rr[j].k;
+          if constexpr (HV) vd[i] = rr[j].v;
+        }
       }
+      __syncthreads();
+      continue;
+    }
+    // one counting pass on the top fb bits of key - kmin (2^fb bins, n to 2n
+    // of them): histogram, bin starts, placement in arbitrary order inside a
+    // bin; the write-out then ranks each record among its bin's records by
+    // (key, original index), which gives the stable order
+    const int fb = min(max(bitlen64((uint64_t)(n - 1)), 9), S::FIN_FB);
+    const int psh = fb - 9;                 // log2 bins per thread
+    const int per = 1 << psh;
+    const int bsh = bitlen64(span) > fb ? bitlen64(span) - fb : 0;
+    // bin of a key (32-bit arithmetic for 32-bit keys)
+    auto bin_of = [&](K k) -> unsigned {
+      if constexpr (sizeof(K) == 4) return (unsigned)(k - kmin) >> bsh;
+      else return (unsigned)((uint64_t)(k - kmin) >> bsh);
+    };
+    {
+      uint4 *z = (uint4 *)bins;
+      const int nw = ((1 << fb) + NT) / 4;
+      for (int i = threadIdx.x; i < nw; i += NT) z[i] = make_uint4(0, 0, 0, 0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < S::FIN_IT; ++j) {
+      const int i = j * NT + threadIdx.x;
+      if (j < R && i < n) {
+        const unsigned b = bin_of(rr[j].k);
+        atomicAdd(&bins[b + (b >> psh)], 1u);
+      }
+    }
+    __syncthreads();
+    {
+      // thread t owns bins [t per, (t+1) per), stored at t (per + 1)
+      unsigned *mb = bins + threadIdx.x * (per + 1);
+      unsigned cnt[S::FIN_PER];
+      unsigned sum = 0, mx = 0;
+#pragma unroll
+      for (int q = 0; q < S::FIN_PER; ++q) {
+        cnt[q] = q < per ? mb[q] : 0u;
+        sum += cnt[q];
+        mx = max(mx, cnt[q]);
+      }
+      mx = __reduce_max_sync(0xffffffffu, mx);
+      if (lane == 0) atomicMax(cmax_sh, mx);
+      unsigned tot;
+      unsigned run = block_excl_scan<unsigned>(sum, sh, tot);
+#pragma unroll
+      for (int q = 0; q < S::FIN_PER; ++q) {
+        if (q < per) mb[q] = run;
+        run += cnt[q];
+      }
+    }
+    __syncthreads();
+    if (*cmax_sh <= (unsigned)S::FIN_CMAX) {
+#pragma unroll
+      for (int j = 0; j < S::FIN_IT; ++j) {
+        const int i = j * NT + threadIdx.x;
+        if (j < R && i < n) {
+          const unsigned b = bin_of(rr[j].k);
+          const unsigned p = atomicAdd(&bins[b + (b >> psh)], 1u);
+          rb[p] = rr[j];
+          if constexpr (HV) ix[p] = (uint16_t)i;
+        }
+      }
+      __syncthreads();
+      // bins now hold their ends: bin b is [end(b-1), end(b))
+      for (int p = threadIdx.x; p < n; p += NT) {
+        const RecT x = rb[p];
+        const unsigned b = bin_of(x.k);
+        const unsigned e0 = bins[b + (b >> psh)];
+        const unsigned s0 = b ? bins[(b - 1) + ((b - 1) >> psh)] : 0u;
+        unsigned r = (unsigned)p;
+        if (e0 - s0 > 1) {
+          r = s0;
+          if constexpr (HV) {
+            const uint16_t xi = ix[p];
+            for (unsigned q = s0; q < e0; ++q) {
+              const K y = rb[q].k;
+              r += (y < x.k || (y == x.k && ix[q] < xi)) ? 1u : 0u;
+            }
+          } else {
+            for (unsigned q = s0; q < e0; ++q) {
+              const K y = rb[q].k;
+              r += (y < x.k || (y == x.k && q < (unsigned)p)) ? 1u : 0u;
+            }
+          }
+        }
+        kd[r] = x.k;
+        if constexpr (HV) vd[r] = x.v;
+      }
+      __syncthreads();
+      continue;
+    }
+    // a bin with many equal-prefix keys: stable LSD passes over the task's
+    // hi bits (the bins are no longer read)
+    my_lsd += 1;
+#pragma unroll
+    for (int j = 0; j < S::FIN_IT; ++j) {
+      const int i = j * NT + threadIdx.x;
+      if (j < R && i < n) ra[i] = rr[j];
     }
     __syncthreads();
     RecT *rin = ra, *rout = rb;
     const int passes = (tk.hi + FIN_DIG - 1) / FIN_DIG;
     // every warp ranks R consecutive rounds of 32 items (warp w covers
     // [32 R w, 32 R (w+1)) of the current order), R as small as n allows
-    const int R = (n + NT - 1) / NT;
     for (int q = 0; q < passes; ++q) {
       const int shift = q * FIN_DIG;
       const int bits = tk.hi - shift < FIN_DIG ? tk.hi - shift : FIN_DIG;
@@ -863,7 +1099,7 @@ __device__ void phase_finish(const Params &P, int level, unsigned char *smem) {
         dr[j] = 0xFFFFFFFFu;
         if (j < R && w * 32 * R + j * 32 < n) {  // warp-uniform
           unsigned d = 1u << FIN_DIG;  // dummy digit
-          if (i < n) d = (unsigned)((uint64_t)rin[i].k >> shift) & dmask;
+          if (i < n) d = (unsigned)(((uint64_t)rin[i].k - tk.base) >> shift) & dmask;
           const unsigned r = warp_rank_slots(d, myfs, mywc);
           dr[j] = (d << 16) | r;
         }
@@ -897,6 +1133,10 @@ __device__ void phase_finish(const Params &P, int level, unsigned char *smem) {
         if (j < R && i < n) {
           const unsigned d = dr[j] >> 16;
           const unsigned pp = doff[d] + wcnt[w * FIN_NB + d] + (dr[j] & 0xFFFFu);
+          if (d >= (1u << FIN_DIG) || pp >= (unsigned)n) {
+            bad = 1u + pp;
+            continue;
+          }
           rout[pp] = rin[i];
         }
       }
@@ -911,14 +1151,14 @@ __device__ void phase_finish(const Params &P, int level, unsigned char *smem) {
       if constexpr (HV) vdst[tk.start + i] = x.v;
     }
     __syncthreads();
-    my_recs += n;
-    my_tasks += 1;
   }
   if (threadIdx.x == 0) {
     if (my_tasks) atomic_add_ll(&c->st_fin_tasks, my_tasks);
     if (my_recs) atomic_add_ll(&c->st_fin_records, my_recs);
     if (my_copy) atomic_add_ll(&c->st_copy_records, my_copy);
+    if (my_lsd) atomic_add_ll(&c->st_fin_lsd_tasks, my_lsd);
   }
+  if (bad) check_failed(P, 2, bad - 1u, level);
 }
 
 // ------------------------------------------------------------------ merge
@@ -934,6 +1174,10 @@ __device__ void phase_merge_prep(const Params &P, int level, unsigned char *smem
   long long *sh = (long long *)dts_smem;
   for (int64_t zi = z0 + blockIdx.x; zi < z1; zi += gridDim.x) {
     const MZone Z = ldcg_obj(&P.zones[zi]);
+    if (Z.m < 0 || Z.m > HASH_HW / 2 || Z.obuf > 1) {
+      if (threadIdx.x == 0) check_failed(P, 8, zi, Z.m);
+      continue;
+    }
     const K *B0 = (const K *)P.keys[Z.obuf ^ 1] + Z.zs;
     const int q = threadIdx.x;
     long long sz = 0, lb = 0;
@@ -983,6 +1227,12 @@ __device__ void phase_merge(const Params &P, int level, unsigned char *smem) {
       __syncthreads();
       const int q = threadIdx.x;
       long long sz = 0;
+      if (Zs->m < 0 || Zs->m > HASH_HW / 2) {
+        if (q == 0) check_failed(P, 8, a, Zs->m);
+        __syncthreads();
+        if (q == 0) Zs->m = 0;
+        __syncthreads();
+      }
       if (q < Zs->m) {
         sz = __ldcg((const long long *)&P.mh_sizes[Zs->mh + q]);
         hs[q] = __ldcg((const long long *)&P.mh_start[Zs->mh + q]);
@@ -1067,10 +1317,18 @@ __device__ __forceinline__ void write_stats(const Params &P, unsigned long long 
     d->copy_records = ld_cg64(&c->st_copy_records);
     d->merge_zones = (int64_t)(__ldcg(&c->zone_alloc) >> 40);
     d->merge_records = ld_cg64(&c->st_merge_records);
-    d->learned_fixup_records = 0;
-    d->learned_fixup_steps = 0;
-    d->learned_cv = 0;
-    d->learned_mom = 0;
+    d->learned_fixup_records = ld_cg64(&c->st_fix_records);
+    d->learned_fixup_steps = ld_cg64(&c->st_fix_steps);
+    const long long nzb = ld_cg64(&c->st_bnz);
+    const double bsum = __ldcg(&c->st_bsum), bsq = __ldcg(&c->st_bsq);
+    const double mean = nzb > 0 ? bsum / (double)nzb : 0.0;
+    const double var = nzb > 0 ? bsq / (double)nzb - mean * mean : 0.0;
+    d->learned_cv = mean > 0 ? sqrt(var > 0 ? var : 0.0) / mean : 0.0;
+    d->learned_mom = mean > 0 ? (double)ld_cg64(&c->st_bmax) / mean : 0.0;
+    d->fin_lsd_tasks = ld_cg64(&c->st_fin_lsd_tasks);
+    d->check_site = ld_cg64(&c->dbg[0]);
+    d->check_values[0] = ld_cg64(&c->dbg[1]);
+    d->check_values[1] = ld_cg64(&c->dbg[2]);
     for (int k = 0; k < 7; ++k) d->phase_ms[k] = (double)c->t_phase[k] * 1e-6;
     d->phase_ms[7] = tbeg ? (double)(gtimer() - tbeg) * 1e-6 : 0.0;
   }

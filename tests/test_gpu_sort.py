@@ -100,6 +100,25 @@ def test_edge_sizes_kv(G, n, dtype):
     check(G, keys, vals)
 
 
+@pytest.mark.parametrize("mult", [2, 5, 16, 17, 40])
+@pytest.mark.parametrize("dtype", [np.uint32, np.uint64])
+def test_base_case_ties(G, mult, dtype):
+    # keys repeated `mult` times in shuffled order: equal keys share a bin of
+    # the one-pass base case and must come out in input order (more than 16
+    # in a bin takes the LSD passes instead)
+    rs = np.random.RandomState(mult)
+    for n in (4800, 250_000):
+        distinct = gen.family("uniform", n // mult + 1, dtype, seed=mult)
+        keys = np.repeat(distinct, mult)[:n]
+        keys = keys[rs.permutation(n)].copy()
+        vals = gen.iota(n, dtype)
+        check(G, keys, vals)
+        G.set_options(heavy_detection=-1)
+        check(G, keys, vals)
+        G.reset_options()
+        check(G, keys, None)
+
+
 def test_n_zero_is_noop(G):
     keys = np.zeros(0, dtype=np.uint32)
     st = G.launch(None, None, 0, dts.DTSORT_OP_U32_KV)
