@@ -464,19 +464,39 @@ __device__ __forceinline__ unsigned learned_zone_exact(K key, const K *spl, int 
   return (unsigned)lo;
 }
 
+// What GetBucketId needs of a subproblem, copied into registers once per
+// subproblem (the shared-memory tables are read only for the lookups).
+struct BucketCtx {
+  uint64_t base, hmask;  // key - base, restricted to the unsorted bits
+  int lo, t, nb, hbits, learned, B;
+};
+
+template <typename K>
+__device__ __forceinline__ BucketCtx bucket_ctx(const SegTables<K> &T) {
+  BucketCtx x;
+  x.base = T.base;
+  x.hmask = lowmask(T.hi);
+  x.lo = T.info.lo;
+  x.t = T.info.t;
+  x.nb = T.info.nb;
+  x.hbits = T.info.hbits;
+  x.learned = T.info.learned;
+  x.B = 1 << T.info.gamma;
+  return x;
+}
+
 // GetBucketId (Alg. 2): heavy keys through H, overflow past the sampled key
 // range, light keys through L by their MSD zone (or learned zone).
 // lid/hk/hid/spl/tab: the tables in shared memory.
 template <typename K>
-__device__ __forceinline__ unsigned bucket_of(const SegTables<K> &T, const int32_t *lid,
+__device__ __forceinline__ unsigned bucket_of(const BucketCtx &X, const int32_t *lid,
                                               const K *hk, const uint16_t *hid, K key,
                                               const K *spl = nullptr,
                                               const float *tab = nullptr,
                                               unsigned *steps = nullptr) {
-  const SegInfo &I = T.info;
-  if (I.hbits) {
-    const uint32_t cap1 = (1u << I.hbits) - 1u;
-    uint32_t s = hash_slot<K>(key, I.hbits);
+  if (X.hbits) {
+    const uint32_t cap1 = (1u << X.hbits) - 1u;
+    uint32_t s = hash_slot<K>(key, X.hbits);
     while (true) {
       const uint16_t id = hid[s];
       if (id == HEMPTY) break;
@@ -484,15 +504,21 @@ __device__ __forceinline__ unsigned bucket_of(const SegTables<K> &T, const int32
       s = (s + 1) & cap1;
     }
   }
-  if (I.learned) {
+  if (X.learned) {
     unsigned st;
-    const unsigned z = learned_zone<K>(key, spl, tab, 1 << I.gamma, &st);
+    const unsigned z = learned_zone<K>(key, spl, tab, X.B, &st);
     if (steps) *steps = st;
     return (unsigned)lid[z];
   }
-  const uint64_t m = ((uint64_t)key - T.base) & lowmask(T.hi);
-  if (I.t < 64 && (m >> I.t) != 0) return (unsigned)(I.nb - 1);
-  return (unsigned)lid[m >> I.lo];
+  if constexpr (sizeof(K) == 4) {
+    const uint32_t m = ((uint32_t)key - (uint32_t)X.base) & (uint32_t)X.hmask;
+    if (X.t < 32 && (m >> X.t) != 0) return (unsigned)(X.nb - 1);
+    return (unsigned)lid[m >> X.lo];
+  } else {
+    const uint64_t m = ((uint64_t)key - X.base) & X.hmask;
+    if (X.t < 64 && (m >> X.t) != 0) return (unsigned)(X.nb - 1);
+    return (unsigned)lid[m >> X.lo];
+  }
 }
 
 template <typename K>

@@ -451,6 +451,7 @@ __device__ void phase_hist(const Params &P, int level, unsigned char *smem) {
     const unsigned gmask = (1u << (T.info.t - T.info.lo)) - 1u;
     const bool fast = T.info.hbits == 0 && T.info.t >= T.hi && !T.info.learned;
     const uint64_t kbase = T.base;
+    const BucketCtx X = bucket_ctx<K>(T);
     const int64_t lr = r - T.info.blk0;
     if (lr % S::CH == 0) {  // this chunk's look-back status starts empty
       const int64_t row = T.info.soff + (lr / S::CH) * nb;
@@ -478,17 +479,27 @@ __device__ void phase_hist(const Params &P, int level, unsigned char *smem) {
           // b <= gmask < nb: the tables were checked when loaded
           if (i < tn) atomicAdd(&cnt[fast_digit<K>(key[j], kbase, lo, gmask)], 1u);
         }
-      } else {
+      } else if (X.learned) {
 #pragma unroll
         for (int j = 0; j < S::ITEMS; ++j) {
           const int i = w * 32 * S::ITEMS + j * 32 + lane;
           if (i < tn) {
             unsigned st = 0;
-            const unsigned b = bucket_of<K>(T, lid_s, hk_s, hid_s, key[j], spl_s, tab_s, &st);
+            const unsigned b = bucket_of<K>(X, lid_s, hk_s, hid_s, key[j], spl_s, tab_s, &st);
             if (b < (unsigned)nb) atomicAdd(&cnt[b], 1u);
             else bad = b;
             fix_recs += st != 0;
             fix_steps += st;
+          }
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < S::ITEMS; ++j) {
+          const int i = w * 32 * S::ITEMS + j * 32 + lane;
+          if (i < tn) {
+            const unsigned b = bucket_of<K>(X, lid_s, hk_s, hid_s, key[j]);
+            if (b < (unsigned)nb) atomicAdd(&cnt[b], 1u);
+            else bad = b;
           }
         }
       }
@@ -743,11 +754,12 @@ __device__ void phase_scatter(const Params &P, int level, unsigned char *smem) {
     const unsigned gmask = (1u << (T.info.t - T.info.lo)) - 1u;
     const bool fast = T.info.hbits == 0 && T.info.t >= T.hi && !T.info.learned;
     const uint64_t kbase = T.base;
+    const BucketCtx X = bucket_ctx<K>(T);
     const int64_t lr = r - T.info.blk0;
-    const unsigned *X = P.cmat + T.info.coff + lr * nb;
+    const unsigned *Xr = P.cmat + T.info.coff + lr * nb;  // this block's offsets
     for (int b = threadIdx.x; b < nb; b += NT)
       base[b] = (unsigned)(__ldcg((const long long *)&P.bstart[T.info.boff + b]) - T.start) +
-                __ldcg(X + b);
+                __ldcg(Xr + b);
     const int64_t b0 = T.start + lr * (int64_t)P.blk_tiles * S::TILE;
     const int64_t brem = T.start + T.size - b0;
     K *dseg = dst + T.start;
@@ -784,7 +796,7 @@ __device__ void phase_scatter(const Params &P, int level, unsigned char *smem) {
         for (int j = 0; j < S::ITEMS; ++j) {
           const int i = w * 32 * S::ITEMS + j * 32 + lane;
           const unsigned b =
-              i < tn ? bucket_of<K>(T, lid_s, hk_s, hid_s, key[j], spl_s, tab_s) : (unsigned)nb;
+              i < tn ? bucket_of<K>(X, lid_s, hk_s, hid_s, key[j], spl_s, tab_s) : (unsigned)nb;
           br[j] = (b << 16) | warp_rank_slots(b, myslot, mywc);
         }
       }
