@@ -339,7 +339,7 @@ def run_ours(args):
                      "frac": achieved / peak, "traffic": None,
                      "peak_kind": peak_kind, "bytes_per_record": B_ALG[args.op],
                      "kernel": "dts::dtsort_kernel (one persistent launch per sort)"},
-        "gpu_launches": args.steps,
+        "gpu_launches": args.steps * stats["kernel_launches"],
         "clocks": clk.summary(),
         "e2e": e2e,
         "stats": {"levels": stats["levels"], "phase_ms": stats["phase_ms"],
@@ -501,7 +501,7 @@ def run_segmented(args):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
                      "bytes": b_alg},
-        "gpu_launches": args.steps, "clocks": clk.summary(),
+        "gpu_launches": args.steps * stats["kernel_launches"], "clocks": clk.summary(),
         "baseline_separate_calls": base,
         "stats": {"levels": stats["levels"], "phase_ms": stats["phase_ms"],
                   "finisher_tasks": stats["finisher_tasks"]},

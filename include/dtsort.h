@@ -102,11 +102,19 @@ typedef struct {
   int32_t debug_fault;       /* testing only: 1 = the second look-back chunk of
                                 the first distribution never publishes its
                                 status, so its successors' waits expire */
-  int32_t launch_mode;       /* 0: one persistent cooperative launch per sort
-                                (default, no host synchronisation);
+  int32_t launch_mode;       /* 0 (default): for a single array, the levels a
+                                uniformly distributed input of this size needs
+                                run as one launch per phase, queued without
+                                host synchronisation (each phase checks on the
+                                device whether it has work), then one
+                                persistent cooperative launch takes any further
+                                levels and the merges; a segmented call is the
+                                persistent launch alone.  No host
+                                synchronisation; capturable in a CUDA graph.
                                 1: one launch per phase with the level loop on
                                 the host (a profiling aid: every phase appears
-                                as its own kernel; synchronises the stream) */
+                                as its own kernel; synchronises the stream).
+                                2: the persistent launch alone. */
   int32_t block_tiles;       /* rows of the per-level count matrix cover
                                 block_tiles tiles of the scatter (8K 32-bit or
                                 4K 64-bit keys each); 1..8, default 4 */
@@ -144,7 +152,9 @@ typedef struct {
   int64_t finisher_lsd_tasks;     /* base-case buckets that needed the LSD
                                      passes (a one-pass bin held too many
                                      equal-prefix keys) */
-  int64_t reserved[4];
+  int64_t kernel_launches;        /* kernels the last sort call launched
+                                     (host count; memsets not included) */
+  int64_t reserved[3];
 } dtsort_stats;
 
 DTSORT_API const char *dtsort_status_string(dtsort_status s);

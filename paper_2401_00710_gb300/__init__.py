@@ -87,7 +87,8 @@ class dtsort_stats(ctypes.Structure):
                 ("check_site", ctypes.c_int64),
                 ("check_values", ctypes.c_int64 * 2),
                 ("finisher_lsd_tasks", ctypes.c_int64),
-                ("reserved", ctypes.c_int64 * 4)]
+                ("kernel_launches", ctypes.c_int64),
+                ("reserved", ctypes.c_int64 * 3)]
 
     def as_dict(self):
         out = {}

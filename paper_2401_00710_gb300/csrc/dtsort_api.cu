@@ -55,6 +55,7 @@ struct dtsort_handle_s {
   DevStats *d_stats = nullptr;
   KernelShape shape[kOps]{};
   bool shape_ok[kOps]{};
+  int64_t launches = 0;      // kernels launched by the last sort call
 };
 
 namespace {
@@ -170,6 +171,22 @@ int plan_gamma_host(int64_t s, int64_t target, int gmax, int hi, int fin_dig) {
     g = best;
   }
   return g;
+}
+
+// Distribution levels of a uniformly distributed array of n keys of
+// key_bits bits under the device's digit-width rule (an estimate for skewed
+// inputs; the persistent kernel takes any further levels).
+int predict_levels(int64_t n, int key_bits, const Opts &o, int64_t target) {
+  int64_t s = n;
+  int hi = key_bits, lv = 0;
+  while (s > o.cap && hi > 0 && lv < 6) {
+    const int g = plan_gamma_host(s, target, std::min(o.gamma_max, dts::GAMMA_HW), hi,
+                                  dts::FIN_DIG);
+    s = (s + ((int64_t)1 << g) - 1) >> g;
+    hi -= g;
+    ++lv;
+  }
+  return lv;
 }
 
 // Appends the learned-bucketing region to a layout: the model sample (about
@@ -312,6 +329,7 @@ dtsort_status run_sort(dtsort_handle h, int op, void *keys, void *vals, const in
                        int64_t nsegs, int64_t n, void *ws, size_t ws_bytes, cudaStream_t s,
                        bool allow_learned = true) {
   if (!h) return DTSORT_ERR_INVALID_ARG;
+  if (allow_learned) h->launches = 0;  // a top-level call
   if (n < 0 || nsegs < 0) return DTSORT_ERR_INVALID_ARG;
   if (offsets && nsegs == 0) return n == 0 ? DTSORT_OK : DTSORT_ERR_INVALID_ARG;
   if (n == 0) return DTSORT_OK;
@@ -406,6 +424,7 @@ dtsort_status run_sort(dtsort_handle h, int op, void *keys, void *vals, const in
         (e = dts::lrn_splitters(prm, L.lrn_B, kb, w + L.lspl, (float *)(w + L.ltab), s)) !=
             cudaSuccess)
       return DTSORT_ERR_CUDA;
+    h->launches += 4 + 2 * (int64_t)steps;  // gather, features, init, training, boundaries
     P.lrn_B = L.lrn_B;
     P.lrn_spl = w + L.lspl;
     P.lrn_tab = (const float *)(w + L.ltab);
@@ -416,20 +435,27 @@ dtsort_status run_sort(dtsort_handle h, int op, void *keys, void *vals, const in
   if (h->opt.launch_mode == 1) {
     if (!h->ctl_host && cudaMallocHost(&h->ctl_host, sizeof(dts::Ctl)) != cudaSuccess)
       return DTSORT_ERR_CUDA;
+    int cnt = 0;
     switch (op) {
-      case DTSORT_OP_U32: e = dts::launch_split_u32(P, grid, s, h->ctl_host); break;
-      case DTSORT_OP_U32_KV: e = dts::launch_split_u32kv(P, grid, s, h->ctl_host); break;
-      case DTSORT_OP_U64: e = dts::launch_split_u64(P, grid, s, h->ctl_host); break;
-      default: e = dts::launch_split_u64kv(P, grid, s, h->ctl_host); break;
+      case DTSORT_OP_U32: e = dts::launch_split_u32(P, grid, s, h->ctl_host, &cnt); break;
+      case DTSORT_OP_U32_KV: e = dts::launch_split_u32kv(P, grid, s, h->ctl_host, &cnt); break;
+      case DTSORT_OP_U64: e = dts::launch_split_u64(P, grid, s, h->ctl_host, &cnt); break;
+      default: e = dts::launch_split_u64kv(P, grid, s, h->ctl_host, &cnt); break;
     }
+    h->launches += cnt;
     return from_cuda(e);
   }
+  // single arrays: the levels a uniform input needs run as separate phase
+  // launches, the rest (if any) in the persistent kernel
+  const int head = (h->opt.launch_mode == 0 && !offsets)
+                       ? predict_levels(n, 8 * kb, o, L.target) : 0;
   switch (op) {
-    case DTSORT_OP_U32: e = dts::launch_u32(P, grid, s); break;
-    case DTSORT_OP_U32_KV: e = dts::launch_u32kv(P, grid, s); break;
-    case DTSORT_OP_U64: e = dts::launch_u64(P, grid, s); break;
-    default: e = dts::launch_u64kv(P, grid, s); break;
+    case DTSORT_OP_U32: e = dts::launch_u32(P, grid, head, s); break;
+    case DTSORT_OP_U32_KV: e = dts::launch_u32kv(P, grid, head, s); break;
+    case DTSORT_OP_U64: e = dts::launch_u64(P, grid, head, s); break;
+    default: e = dts::launch_u64kv(P, grid, head, s); break;
   }
+  h->launches += 1 + (head > 0 ? 1 + 7 * (int64_t)head : 0);
   return from_cuda(e);
 }
 
@@ -517,7 +543,7 @@ dtsort_status dtsort_set_options(dtsort_handle h, const dtsort_options *opt) {
       (opt->bucketing != DTSORT_BUCKETING_DIGIT && opt->bucketing != DTSORT_BUCKETING_LEARNED) ||
       opt->learned_segments < 0 || opt->learned_train_steps < 0 || opt->wait_limit_ms < 0 ||
       opt->debug_fault < 0 || opt->debug_fault > 1 || opt->launch_mode < 0 ||
-      opt->launch_mode > 1 || opt->block_tiles < 0 || opt->block_tiles > 8)
+      opt->launch_mode > 2 || opt->block_tiles < 0 || opt->block_tiles > 8)
     return DTSORT_ERR_INVALID_ARG;
   h->opt = *opt;
   return DTSORT_OK;
@@ -629,6 +655,7 @@ dtsort_status dtsort_get_stats(dtsort_handle h, dtsort_stats *out) {
   out->learned_bucket_max_over_mean = d.learned_mom;
   for (int k = 0; k < 8; ++k) out->phase_ms[k] = d.phase_ms[k];
   out->finisher_lsd_tasks = d.fin_lsd_tasks;
+  out->kernel_launches = h->launches;
   out->check_site = d.check_site;
   out->check_values[0] = d.check_values[0];
   out->check_values[1] = d.check_values[1];

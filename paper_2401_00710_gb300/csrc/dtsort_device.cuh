@@ -119,7 +119,9 @@ struct Ctl {
   double st_bsum, st_bsq;
   long long st_bmax, st_bnz;
   unsigned long long t_phase[8];
-  unsigned long long t_last;
+  unsigned long long t_last, t_begin;
+  int levels_done;  // levels whose base case ran as a separate launch
+  int pad2_;
 };
 
 // Statistics as the host reads them (mirrors the public struct's prefix).
@@ -256,7 +258,7 @@ __device__ __forceinline__ uint32_t hash_slot(K key, int bits) {
 }
 
 // Grid-wide barrier for a cooperatively launched grid (all CTAs resident).
-static __device__ __noinline__ void grid_sync(const Params &P) {
+static __device__ __forceinline__ void grid_sync(const Params &P) {
   __syncthreads();
   if (threadIdx.x == 0) {
     Ctl *c = P.ctl;

@@ -15,6 +15,11 @@ cudaError_t DTS_CAT(shape_, DTS_NAME)(KernelShape *out) {
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
+  // the per-phase kernel too, here and not at launch (launches may be
+  // captured into a graph)
+  e = cudaFuncSetAttribute(dtsort_phase_kernel<DTS_K, DTS_HV>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
   int nb = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, NT, smem);
   if (e != cudaSuccess) return e;
@@ -27,26 +32,52 @@ cudaError_t DTS_CAT(shape_, DTS_NAME)(KernelShape *out) {
   return cudaSuccess;
 }
 
-cudaError_t DTS_CAT(launch_, DTS_NAME)(const Params &P, int grid, cudaStream_t s) {
-  auto *fn = dtsort_kernel<DTS_K, DTS_HV>;
+// The first `head` levels as separate phase launches (queued, no host
+// synchronisation; each phase checks on the device whether it has work), then
+// the persistent kernel for the remaining levels and the merges.  head = 0:
+// the persistent kernel alone.
+cudaError_t DTS_CAT(launch_, DTS_NAME)(const Params &P, int grid, int head, cudaStream_t s) {
   const size_t smem = smem_bytes<DTS_K, DTS_HV>();
+  cudaError_t e;
+  if (head > 0) {
+    auto *pf = dtsort_phase_kernel<DTS_K, DTS_HV>;  // attributes set by shape_
+    auto run = [&](int phase, int level, int g, int prev) {
+      pf<<<g, NT, smem, s>>>(P, phase, level, 1, prev);
+      return cudaGetLastError();
+    };
+    if ((e = run(KP_SEED, 0, grid, -1)) != cudaSuccess) return e;
+    for (int l = 0; l < head; ++l) {
+      if ((e = run(KP_SETUP, l, 1, l == 0 ? PH_SETUP : PH_FINISH)) != cudaSuccess ||
+          (e = run(KP_SAMPLE, l, grid, PH_SETUP)) != cudaSuccess ||
+          (e = run(KP_HIST, l, grid, PH_SAMPLE)) != cudaSuccess ||
+          (e = run(KP_MSCAN, l, grid, PH_HIST)) != cudaSuccess ||
+          (e = run(KP_SCAN, l, grid, PH_SCAN)) != cudaSuccess ||
+          (e = run(KP_SCATTER, l, grid, PH_SCAN)) != cudaSuccess ||
+          (e = run(KP_FINISH, l, grid, PH_SCATTER)) != cudaSuccess)
+        return e;
+    }
+  }
+  auto *fn = dtsort_kernel<DTS_K, DTS_HV>;
   Params copy = P;
-  void *args[] = {&copy};
+  int lev0 = head;
+  void *args[] = {&copy, &lev0};
   return cudaLaunchCooperativeKernel((const void *)fn, dim3(grid), dim3(NT), args, smem, s);
 }
 
 // One launch per phase; the host reads the control block between levels.
 // ctl_host: pinned host memory for sizeof(Ctl).
 cudaError_t DTS_CAT(launch_split_, DTS_NAME)(const Params &P, int grid, cudaStream_t s,
-                                             void *ctl_host) {
+                                             void *ctl_host, int *launches) {
   auto *fn = dtsort_phase_kernel<DTS_K, DTS_HV>;
   const size_t smem = smem_bytes<DTS_K, DTS_HV>();
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
   Ctl *h = (Ctl *)ctl_host;
+  *launches = 0;
   auto run = [&](int phase, int level, int g) {
-    fn<<<g, NT, smem, s>>>(P, phase, level);
+    fn<<<g, NT, smem, s>>>(P, phase, level, 0, -1);
+    ++*launches;
     return cudaGetLastError();
   };
   auto fetch = [&]() {

@@ -20,9 +20,9 @@ struct KernelShape {
 };
 
 #define DTS_DECLARE(NAME)                                                      \
-  cudaError_t launch_##NAME(const Params &P, int grid, cudaStream_t s);        \
+  cudaError_t launch_##NAME(const Params &P, int grid, int head, cudaStream_t s); \
   cudaError_t launch_split_##NAME(const Params &P, int grid, cudaStream_t s,   \
-                                  void *ctl_host);                             \
+                                  void *ctl_host, int *launches);              \
   cudaError_t shape_##NAME(KernelShape *out);
 #define DTS_DECLARE_SAMPLE(NAME)                                               \
   cudaError_t launch_sample_##NAME(const void *keys, int64_t start,            \

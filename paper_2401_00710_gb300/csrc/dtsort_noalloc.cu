@@ -204,7 +204,8 @@ extern "C" dtsort_status dtsort_u32_kv_noalloc(uint32_t *keys, uint32_t *values,
   P.mhmax = L.mhmax;
   P.dev_status = status_word;
   P.stats = (dts::DevStats *)(w + L.stats);
-  void *args[] = {&P};
+  int lev0 = 0;  // the persistent kernel alone
+  void *args[] = {&P, &lev0};
   const cudaError_t e = cudaLaunchCooperativeKernel(
       (const void *)dts::dtsort_kernel<uint32_t, true>, dim3(D->grid), dim3(dts::NT), args,
       dts::smem_bytes<uint32_t, true>(), s);

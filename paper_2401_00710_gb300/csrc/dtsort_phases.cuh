@@ -1346,71 +1346,18 @@ __device__ __forceinline__ void write_stats(const Params &P, unsigned long long 
   }
 }
 
-template <typename K, bool HV>
-__global__ void __launch_bounds__(NT, 2) dtsort_kernel(const Params P) {
-  unsigned char *smem = dts_smem;
-  Ctl *c = P.ctl;
-  if (blockIdx.x == 0 && threadIdx.x == 0) c->t_last = gtimer();
-  const unsigned long long tbeg = gtimer();
-  phase_seed<K, HV>(P);
-  grid_sync(P);
-  tick(P, PH_SETUP);
-  int level = 0;
-  for (; level < MAXLEV; ++level) {
-    const int p = level & 1;
-    const long long nseg = ld_cg64(&c->nseg[p]);
-    if (level > 0 && nseg == 0) break;
-    if (*(volatile int *)&c->err_snap) break;
-    if (blockIdx.x == 0) phase_setup<K, HV>(P, level, smem);
-    grid_sync(P);
-    tick(P, PH_SETUP);
-    if (*(volatile int *)&c->err_snap) break;  // e.g. a table would overflow
-    if (nseg > 0) {
-      phase_sample<K, HV>(P, level, smem);
-      grid_sync(P);
-      tick(P, PH_SAMPLE);
-      phase_hist<K, HV>(P, level, smem);
-      grid_sync(P);
-      tick(P, PH_HIST);
-      phase_mscan<K, HV>(P, level, smem);
-      grid_sync(P);
-      tick(P, PH_SCAN);
-      if (*(volatile int *)&c->err_snap) break;  // offsets unusable
-      phase_scan<K, HV>(P, level, smem);
-      grid_sync(P);
-      tick(P, PH_SCAN);
-      phase_scatter<K, HV>(P, level, smem);
-      grid_sync(P);
-      tick(P, PH_SCATTER);
-    }
-    phase_finish<K, HV>(P, level, smem);
-    grid_sync(P);
-    tick(P, PH_FINISH);
-  }
-  close_levels(P, level);
-  grid_sync(P);
-  for (int l = level - 1; l >= 0; --l) {
-    if (*(volatile int *)&c->err_snap) break;
-    if (ld_cg64(&c->lvl_zone[l + 1]) == ld_cg64(&c->lvl_zone[l])) continue;
-    phase_merge_prep<K, HV>(P, l, smem);
-    grid_sync(P);
-    phase_merge<K, HV>(P, l, smem);
-    grid_sync(P);
-    tick(P, PH_MERGE);
-  }
-  write_stats(P, tbeg);
-}
-
 // The same phases as separate launches (one phase per launch, the level loop
 // driven by the host).  A profiling aid: every phase shows up as its own
-// kernel launch; the persistent kernel above is the product path.
+// kernel launch; the persistent kernel below is the product path.
 enum {
   KP_SEED = 0, KP_SETUP, KP_SAMPLE, KP_HIST, KP_MSCAN, KP_SCAN, KP_SCATTER, KP_FINISH,
   KP_CLOSE, KP_MERGE_PREP, KP_MERGE, KP_STATS
 };
 
+// One phase (all phases share one body, so that the persistent kernel and
+// the per-phase kernel are compiled alike).
 template <typename K, bool HV>
-__global__ void __launch_bounds__(NT, 2) dtsort_phase_kernel(const Params P, int phase, int level) {
+__device__ __forceinline__ void run_phase(const Params &P, int phase, int level) {
   unsigned char *smem = dts_smem;
   switch (phase) {
     case KP_SEED: phase_seed<K, HV>(P); break;
@@ -1427,6 +1374,127 @@ __global__ void __launch_bounds__(NT, 2) dtsort_phase_kernel(const Params P, int
     case KP_STATS: write_stats(P, 0); break;
     default: break;
   }
+}
+
+// The level loop as a state machine: (phase, level) -> next (phase, level),
+// decided alike by every CTA from the control block after a grid barrier.
+// Returns KP_DONE after the last merge.
+constexpr int KP_DONE = -1;
+__device__ __forceinline__ int next_phase(const Params &P, int phase, int &level) {
+  Ctl *c = P.ctl;
+  const bool err = *(volatile int *)&c->err_snap != 0;
+  switch (phase) {
+    case KP_SEED:
+      level = 0;
+      return KP_SETUP;
+    case KP_SETUP: {
+      if (err) return KP_CLOSE;
+      const long long nseg = ld_cg64(&c->nseg[level & 1]);
+      return nseg > 0 ? KP_SAMPLE : KP_FINISH;
+    }
+    case KP_SAMPLE: return KP_HIST;
+    case KP_HIST: return KP_MSCAN;
+    case KP_MSCAN: return err ? KP_CLOSE : KP_SCAN;
+    case KP_SCAN: return KP_SCATTER;
+    case KP_SCATTER: return KP_FINISH;
+    case KP_FINISH: {
+      ++level;
+      if (level >= MAXLEV || err) return KP_CLOSE;
+      return ld_cg64(&c->nseg[level & 1]) == 0 ? KP_CLOSE : KP_SETUP;
+    }
+    case KP_CLOSE:
+    case KP_MERGE: {
+      // merges run from the deepest level up; levels without zones are skipped
+      int l = phase == KP_CLOSE ? *(volatile int *)&c->nlevels - 1 : level - 1;
+      while (l >= 0 && ld_cg64(&c->lvl_zone[l + 1]) == ld_cg64(&c->lvl_zone[l])) --l;
+      if (l < 0 || err) return KP_DONE;
+      level = l;
+      return KP_MERGE_PREP;
+    }
+    case KP_MERGE_PREP: return KP_MERGE;
+    default: return KP_DONE;
+  }
+}
+
+// Which phase-time bucket of the stats a phase's time goes to.
+__device__ __forceinline__ int phase_kind(int phase) {
+  switch (phase) {
+    case KP_SAMPLE: return PH_SAMPLE;
+    case KP_HIST: return PH_HIST;
+    case KP_MSCAN:
+    case KP_SCAN: return PH_SCAN;
+    case KP_SCATTER: return PH_SCATTER;
+    case KP_FINISH: return PH_FINISH;
+    case KP_MERGE_PREP:
+    case KP_MERGE: return PH_MERGE;
+    default: return PH_SETUP;
+  }
+}
+
+// The persistent kernel.  lev0 = 0: the whole sort from the seed phase.
+// lev0 > 0: the first levels already ran as separate phase launches; start
+// at the first level they did not finish (or close if nothing is left).
+template <typename K, bool HV>
+__global__ void __launch_bounds__(NT, 2) dtsort_kernel(const __grid_constant__ Params P,
+                                                       int lev0) {
+  // (phase, level) live in shared memory between phases, so that no register
+  // is held across them
+  __shared__ int st_phase, st_level;
+  Ctl *c = P.ctl;
+  if (threadIdx.x == 0) {
+    if (lev0 == 0) {
+      st_phase = KP_SEED;
+      st_level = 0;
+      if (blockIdx.x == 0) c->t_last = c->t_begin = gtimer();
+    } else {
+      const int l = *(volatile int *)&c->levels_done;
+      st_level = l;
+      st_phase = (*(volatile int *)&c->error || (l > 0 && ld_cg64(&c->nseg[l & 1]) == 0))
+                     ? KP_CLOSE : KP_SETUP;
+      if (blockIdx.x == 0) tick(P, PH_FINISH);
+    }
+  }
+  __syncthreads();
+  while (true) {
+    const int phase = *(volatile int *)&st_phase;
+    int level = *(volatile int *)&st_level;
+    if (phase == KP_DONE) break;
+    run_phase<K, HV>(P, phase, level);
+    grid_sync(P);
+    tick(P, phase_kind(phase));
+    const int next = next_phase(P, phase, level);
+    if (threadIdx.x == 0) {
+      *(volatile int *)&st_phase = next;
+      *(volatile int *)&st_level = level;
+    }
+    __syncthreads();
+  }
+  write_stats(P, c->t_begin);
+}
+
+// One phase per launch.  guard = 1 (launches queued without the host reading
+// the control block): a phase of a level that has no subproblems, or any
+// phase after an error, returns at once; the base case of a level records
+// that the level is done.  prev_kind >= 0: the phase-time bucket the time
+// since the previous launch's start goes to.
+template <typename K, bool HV>
+__global__ void __launch_bounds__(NT, 2) dtsort_phase_kernel(const __grid_constant__ Params P,
+                                                             int phase, int level, int guard,
+                                                             int prev_kind) {
+  Ctl *c = P.ctl;
+  if (guard) {
+    if (*(volatile int *)&c->error) return;
+    if (phase >= KP_SETUP && phase <= KP_FINISH && level > 0 &&
+        ld_cg64(&c->nseg[level & 1]) == 0)
+      return;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (phase == KP_SEED) c->t_last = c->t_begin = gtimer();
+    else if (prev_kind >= 0) tick(P, prev_kind);
+  }
+  run_phase<K, HV>(P, phase, level);
+  if (guard && phase == KP_FINISH && blockIdx.x == 0 && threadIdx.x == 0)
+    c->levels_done = level + 1;
 }
 
 // ---------------------------------------------------- sampler diagnostic

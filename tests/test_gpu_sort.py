@@ -174,15 +174,51 @@ def test_options_do_not_change_output(G, opts):
         check(G, keys, vals)
 
 
-def test_phase_launch_mode_matches(G):
-    # one launch per phase (profiling aid) runs the same phases
+@pytest.mark.parametrize("mode", [1, 2])
+def test_launch_modes_match(G, mode):
+    # 1: one launch per phase, host-driven (profiling aid); 2: the persistent
+    # kernel alone; the default (0) queues the predicted levels as phase
+    # launches and hands the rest to the persistent kernel
     n = 1_500_000
-    for name in ("zipf1.2", "uniform"):
+    for name in ("zipf1.2", "uniform", "distinct10"):
         keys = gen.family(name, n, np.uint32, seed=14)
         vals = gen.iota(n, np.uint32)
-        G.set_options(launch_mode=1)
+        G.set_options(launch_mode=mode)
         st = check(G, keys, vals)
         assert st["levels"] >= 1
+        if mode == 2:
+            assert st["kernel_launches"] == 1
+        else:
+            assert st["kernel_launches"] > 7
+    G.reset_options()
+
+
+@pytest.mark.parametrize("name,dtype", [("uniform", np.uint32), ("zipf1.2", np.uint32),
+                                        ("bitexp", np.uint64), ("distinct10", np.uint32)])
+def test_queued_levels_capture_and_replay(G, name, dtype):
+    # the default single-array launch sequence has no host synchronisation:
+    # it is captured into a CUDA graph and replayed; inputs that need fewer
+    # levels than predicted (10 keys) or more (skewed) come out right
+    n = 3_000_017
+    keys = gen.family(name, n, dtype, seed=21)
+    vals = gen.iota(n, dtype)
+    op = gpu_util.op_of(keys, vals)
+    pk = gpu_util.to_dev(keys, torch, G.dev)
+    pv = gpu_util.to_dev(vals, torch, G.dev)
+    k, v = pk.clone(), pv.clone()
+    G.workspace(op, n)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        assert G.launch(k, v, n, op) == dts.DTSORT_OK
+    ek, ev = oracle.stable_sort(keys, vals)
+    for _ in range(2):
+        k.copy_(pk)
+        v.copy_(pv)
+        graph.replay()
+        torch.cuda.synchronize()
+        assert G.device_status() == dts.DTSORT_OK
+        gpu_util.assert_same(gpu_util.from_dev(k, dtype), gpu_util.from_dev(v, dtype), ek, ev)
 
 
 # --------------------------------------------------------------- segmented
