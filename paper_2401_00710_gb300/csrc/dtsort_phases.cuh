@@ -61,6 +61,18 @@ struct Carve {
   }
 };
 
+// Bytes of the scatter's shared area: ranking slots, or a staged tile (keys
+// with their destinations, or keys with their values).
+template <typename K, bool HV>
+__host__ __device__ constexpr int scatter_area() {
+  using S = Shape<K, HV>;
+  constexpr int slots = 4 * NWARP * NB_PAD;
+  constexpr int kd = S::TILE * (int)sizeof(K) + 4 * S::TILE;
+  constexpr int kv = HV ? 2 * S::TILE * (int)sizeof(K) : 0;
+  constexpr int m = slots > kd ? slots : kd;
+  return m > kv ? m : kv;
+}
+
 template <typename K, bool HV>
 constexpr size_t smem_bytes() {
   using S = Shape<K, HV>;
@@ -71,9 +83,7 @@ constexpr size_t smem_bytes() {
   sc += 16 + sizeof(K) * HASH_HW + 16 + 2 * HASH_HW;  // hash
   sc += 16 + 2 * (size_t)NWARP * NB_PAD;           // warp counters
   sc += 4 * (16 + 4 * NB_PAD);                     // tile counts/offsets, bases
-  const size_t stage_b = (size_t)S::TILE * sizeof(K) + 4 * (size_t)S::TILE;
-  const size_t slot_b = 4 * (size_t)NWARP * NB_PAD;
-  sc += 16 + (slot_b > stage_b ? slot_b : stage_b);  // rank slots / staged tile
+  sc += 16 + (size_t)scatter_area<K, HV>();  // rank slots / staged tile
   sc += 16 + 8 * (NWARP + 1) + 256;
   sc += 16 + sizeof(K) * (1 << GAMMA_HW) + 16 + 4 * (LRN_TAB_N + 1);  // learned tables
   // base case
@@ -723,9 +733,9 @@ __device__ void phase_scatter(const Params &P, int level, unsigned char *smem) {
   unsigned *sh = cv.take<unsigned>(NWARP + 1);
   K *spl_s = cv.take<K>(1 << GAMMA_HW);
   float *tab_s = cv.take<float>(LRN_TAB_N + 1);
-  // ranking slots and the staged tile share one area (never live together)
-  constexpr int AREA = (4 * NWARP * NB_PAD > S::TILE * (int)sizeof(K) + 4 * S::TILE)
-                           ? 4 * NWARP * NB_PAD : S::TILE * (int)sizeof(K) + 4 * S::TILE;
+  // ranking slots and the staged tile share one area (never live together);
+  // the staged tile is keys + destinations, or keys + values on the fast path
+  constexpr int AREA = scatter_area<K, HV>();
   unsigned char *area = cv.take<unsigned char>(AREA);
   unsigned *slots = (unsigned *)area;
   K *stage = (K *)area;
@@ -827,6 +837,47 @@ __device__ void phase_scatter(const Params &P, int level, unsigned char *smem) {
         base[b] += tcnt[b];
       }
       __syncthreads();
+      if (fast) {
+        // keys and values staged side by side in bucket order; the write-out
+        // takes each record's bucket again from its key (a digit), so no
+        // destination array is kept and both arrays go out in one pass
+        K *stage_v = (K *)(area + S::TILE * sizeof(K));
+#pragma unroll
+        for (int j = 0; j < S::ITEMS; ++j) {
+          const int i = w * 32 * S::ITEMS + j * 32 + lane;
+          if (i < tn) {
+            const unsigned b = br[j] >> 16;
+            const unsigned pj = toff[b] + wcnt[w * NB_PAD + b] + (br[j] & 0xFFFFu);
+            if (b >= (unsigned)nb || pj >= (unsigned)tn) {
+              bad = 1u + pj;
+              br[j] = 0xFFFFFFFFu;
+              continue;
+            }
+            stage[pj] = key[j];
+            br[j] = pj;
+          }
+        }
+        if constexpr (HV) {
+#pragma unroll
+          for (int j = 0; j < S::ITEMS; ++j) {
+            const int i = w * 32 * S::ITEMS + j * 32 + lane;
+            if (i < tn && br[j] != 0xFFFFFFFFu) stage_v[br[j]] = ld_key<K>(vsrc + tbase + i);
+          }
+        }
+        __syncthreads();
+        for (int q = threadIdx.x; q < tn; q += NT) {
+          const K k = stage[q];
+          const unsigned d = gbase[fast_digit<K>(k, kbase, lo, gmask)] + (unsigned)q;
+          if (d < seg_size) {
+            dseg[d] = k;
+            if constexpr (HV) vdseg[d] = stage_v[q];
+          } else {
+            bad = 1u + d;
+          }
+        }
+        __syncthreads();
+        continue;
+      }
       // stage keys in bucket order, then write each bucket's run contiguously;
       // br[j] becomes the item's slot in the staged tile
 #pragma unroll
