@@ -131,6 +131,28 @@ def dist_env():
     return rank, world, local
 
 
+# ---- N > 1: independent replicas (every rank sorts its own array) ----------
+def replica_seed(seed, rank):
+    """Each rank sorts a different seeded array of the same workload."""
+    return seed + rank
+
+
+def replica_ms(ms, world, device=None):
+    """Time of one step of the whole job: the slowest rank's (max over ranks)."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as tdist
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(n_per_rank, world, ms):
+    """Whole-job throughput: the records all ranks sorted, per second."""
+    return world * n_per_rank / (ms / 1e3)
+
+
 def key_dtype(op):
     return np.uint32 if op.startswith("u32") else np.uint64
 
@@ -222,7 +244,7 @@ def run_ours(args):
     tdt = torch.int32 if kbytes == 4 else torch.int64
     # inputs: generated on the host into pinned memory, one pristine device copy
     hk = torch.empty(n, dtype=tdt, pin_memory=True)
-    gen.fill_family(args.dist, hk.data_ptr(), n, kd, seed=args.seed + rank)
+    gen.fill_family(args.dist, hk.data_ptr(), n, kd, seed=replica_seed(args.seed, rank))
     hv = None
     if has_v:
         hv = torch.empty(n, dtype=tdt, pin_memory=True)
@@ -287,12 +309,7 @@ def run_ours(args):
     if st != 0:
         raise RuntimeError("device: " + device_error_text(h, st))
     ms = [a.elapsed_time(b) for a, b in ev]
-    ms_step = sum(ms) / len(ms)
-    if world > 1:
-        import torch.distributed as tdist
-        t = torch.tensor([ms_step], device=dev)
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-        ms_step = float(t.item())
+    ms_step = replica_ms(sum(ms) / len(ms), world, dev)
     stats = dts.dtsort_get_stats(h).as_dict()
     # ---- end to end: host buffers in, sorted host buffers out ----
     e2e = None
@@ -315,9 +332,9 @@ def run_ours(args):
             t1.record(stream)
             barrier()
             e_ms.append(t0.elapsed_time(t1))
-        e_ms_step = sum(e_ms) / len(e_ms)
+        e_ms_step = replica_ms(sum(e_ms) / len(e_ms), world, dev)
         by = n * (kbytes * (2 if has_v else 1))
-        e2e = {"value": world * n / (e_ms_step / 1e3), "unit": "keys/s",
+        e2e = {"value": job_rate(n, world, e_ms_step), "unit": "keys/s",
                "h2d_bytes_per_step": by, "d2h_bytes_per_step": by,
                "ms_per_step": e_ms_step}
     if rank != 0:
@@ -326,7 +343,7 @@ def run_ours(args):
     b_alg = B_ALG[args.op] * n
     achieved = b_alg / (ms_step / 1e3) / 1e9
     line = {
-        "metric": METRIC, "value": world * n / (ms_step / 1e3), "unit": "keys/s",
+        "metric": METRIC, "value": job_rate(n, world, ms_step), "unit": "keys/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": args.op, "data": "synthetic",
@@ -384,6 +401,9 @@ def run_segmented(args):
     import paper_2401_00710_gb300 as dts
 
     rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as tdist
+        tdist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
     total = None if args.seg_total == "literal" else float(args.seg_total)
@@ -393,7 +413,8 @@ def run_segmented(args):
     nseg = len(off) - 1
     hk = torch.empty(n, dtype=torch.int32, pin_memory=True)
     hv = torch.empty(n, dtype=torch.int32, pin_memory=True)
-    gen.fill_segmented_u32(hk.data_ptr(), hv.data_ptr(), off, fam, seed=args.seed + rank)
+    gen.fill_segmented_u32(hk.data_ptr(), hv.data_ptr(), off, fam,
+                           seed=replica_seed(args.seed, rank))
     pk, pv = hk.to(dev), hv.to(dev)
     k, v = torch.empty_like(pk), torch.empty_like(pv)
     o = torch.from_numpy(off).to(dev)
@@ -460,8 +481,12 @@ def run_segmented(args):
             ms.append(a.elapsed_time(b))
         return sum(ms) / len(ms), ms
 
+    if world > 1:
+        torch.cuda.synchronize(dev)
+        tdist.barrier()
     with ClockSampler(local) as clk:
         ms_step, ms_list = timed(step, args.steps, args.warmup)
+    ms_step = replica_ms(ms_step, world, dev)
     st = dts.dtsort_last_device_error(h, sp)
     if st != 0:
         raise RuntimeError("device: " + device_error_text(h, st))
@@ -484,11 +509,15 @@ def run_segmented(args):
                 "what": "one dtsort_u32_kv call per array, same GPU, same stream"}
         del sizes
     cap = 6144
+    if rank != 0:
+        dts.dtsort_destroy(h)
+        return 0
     b_alg = sum(int(sz) * (4 + segmented_passes(int(sz), cap) * 2 * 8) for sz in np.diff(off))
     peak, peak_kind = peaks()
     achieved = b_alg / (ms_step / 1e3) / 1e9
     line = {
-        "metric": METRIC, "value": n / (ms_step / 1e3), "unit": "keys/s", "n_gpus": 1,
+        "metric": METRIC, "value": job_rate(n, world, ms_step), "unit": "keys/s",
+        "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32kv",
         "data": "synthetic",
