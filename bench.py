@@ -62,6 +62,36 @@ def parse():
     return ap.parse_args()
 
 
+def kernel_source_id():
+    """Short hash of the CUDA sources and the C header (names + contents)."""
+    import glob
+    import hashlib
+    d = os.path.join(ROOT, "paper_2401_00710_gb300", "csrc")
+    files = sorted(glob.glob(os.path.join(d, "*.cu")) + glob.glob(os.path.join(d, "*.cuh")) +
+                   glob.glob(os.path.join(d, "*.h")))
+    files.append(os.path.join(ROOT, "include", "dtsort.h"))
+    h = hashlib.sha256()
+    for f in files:
+        h.update(os.path.basename(f).encode())
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def dram_traffic(op, dist, n):
+    """DRAM bytes of one sort from the committed ncu summary, scaled to n;
+    None when there is none for this workload or the kernels have changed
+    since it was taken."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "dram_traffic.json")) as f:
+            d = json.load(f)
+        if d.get("kernel_source") != kernel_source_id():
+            return None
+        return float(d["%s/%s" % (op, dist)]["bytes_per_record"]) * n
+    except Exception:
+        return None
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -353,9 +383,13 @@ def run_ours(args):
                    "n": n, "dist": args.dist, "l2": "inputs 8+ GB per step >> L2",
                    "parallelism": "replicas" if world > 1 else "single"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak,
+                     "traffic": dram_traffic(args.op, args.dist, n)
+                     if args.bucketing == "digit" else None,
                      "peak_kind": peak_kind, "bytes_per_record": B_ALG[args.op],
-                     "kernel": "dts::dtsort_kernel (one persistent launch per sort)"},
+                     "kernel": "one sort: the per-phase launches of the predicted levels "
+                               "(dts::dtsort_phase_kernel) + the persistent dts::dtsort_kernel; "
+                               "achieved = algorithmic bytes / CUDA-event time of the sort"},
         "gpu_launches": args.steps * stats["kernel_launches"],
         "clocks": clk.summary(),
         "e2e": e2e,
