@@ -56,7 +56,10 @@ def parse():
                     help="segmented: capture the call once, replay it per step")
     ap.add_argument("--baseline-calls", action="store_true",
                     help="segmented: also time one dtsort_u32_kv call per array")
-    ap.add_argument("--bucketing", default="digit", choices=["digit", "learned"])
+    ap.add_argument("--bucketing", default="digit",
+                    choices=["digit", "learned", "learned-always"],
+                    help="learned: model zones when the device's estimate says they pay; "
+                         "learned-always: model zones regardless")
     ap.add_argument("--autotune", action="store_true",
                     help="run the autotuner on the workload first and use its choice")
     return ap.parse_args()
@@ -286,11 +289,12 @@ def run_ours(args):
     op = {"u32kv": dts.DTSORT_OP_U32_KV, "u32": dts.DTSORT_OP_U32,
           "u64kv": dts.DTSORT_OP_U64_KV, "u64": dts.DTSORT_OP_U64}[args.op]
     h = dts.dtsort_create(local)
-    if args.launch_mode or args.bucketing == "learned":
+    if args.launch_mode or args.bucketing != "digit":
         o = dts.dtsort_get_options(h)
         o.launch_mode = args.launch_mode
-        if args.bucketing == "learned":
-            o.bucketing = dts.DTSORT_BUCKETING_LEARNED
+        o.bucketing = {"digit": dts.DTSORT_BUCKETING_DIGIT,
+                       "learned": dts.DTSORT_BUCKETING_LEARNED,
+                       "learned-always": dts.DTSORT_BUCKETING_LEARNED_ALWAYS}[args.bucketing]
         dts.dtsort_set_options(h, o)
     wsb = dts.dtsort_workspace_bytes(h, op, n)
     ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
@@ -379,7 +383,8 @@ def run_ours(args):
         "vs_baseline": None, "dtype": args.op, "data": "synthetic",
         "config": {"workload": "stable sort, %s, n=%d, keys %s seed %d, values = index%s"
                                % (args.op, n, args.dist, args.seed,
-                                  ", learned zones" if args.bucketing == "learned" else ""),
+                                  "" if args.bucketing == "digit"
+                                  else ", bucketing " + args.bucketing),
                    "n": n, "dist": args.dist, "l2": "inputs 8+ GB per step >> L2",
                    "parallelism": "replicas" if world > 1 else "single"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -400,6 +405,8 @@ def run_ours(args):
                   "finisher_lsd_tasks": stats["finisher_lsd_tasks"],
                   "merge_records": stats["merge_records"],
                   "bucketing": args.bucketing,
+                  "learned_zones_used": stats["learned_zones_used"],
+                  "learned_estimate": stats["learned_estimate"],
                   "level0_bucket_cv": stats["learned_bucket_cv"],
                   "level0_bucket_max_over_mean": stats["learned_bucket_max_over_mean"],
                   "fixup_records": stats["learned_fixup_records"],

@@ -76,7 +76,11 @@ typedef enum {
 
 typedef enum {
   DTSORT_BUCKETING_DIGIT = 0,   /* MSD zones = the next gamma key bits (Alg. 2) */
-  DTSORT_BUCKETING_LEARNED = 1  /* zones from a CDF model fit on the sample */
+  DTSORT_BUCKETING_LEARNED = 1, /* zones from a CDF model fit on a sample, when a
+                                   cost estimate from the sorted sample says they
+                                   save more distribution passes than they cost;
+                                   digit zones otherwise (decided on the device) */
+  DTSORT_BUCKETING_LEARNED_ALWAYS = 2  /* the learned zones without the estimate */
 } dtsort_bucketing;
 
 typedef struct dtsort_handle_s *dtsort_handle;
@@ -154,7 +158,12 @@ typedef struct {
                                      equal-prefix keys) */
   int64_t kernel_launches;        /* kernels the last sort call launched
                                      (host count; memsets not included) */
-  int64_t reserved[3];
+  int64_t learned_zones_used;     /* 1: level 0 used learned zones; 0: digit
+                                     zones (bucketing DIGIT, or LEARNED whose
+                                     estimate chose digits) */
+  double learned_estimate[2];     /* LEARNED: estimated record-passes below
+                                     level 0 with digit zones, and with learned
+                                     zones plus their extra cost */
 } dtsort_stats;
 
 DTSORT_API const char *dtsort_status_string(dtsort_status s);

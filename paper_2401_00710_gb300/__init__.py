@@ -24,7 +24,7 @@ DTSORT_ERR_UNSUPPORTED = 5
 DTSORT_ERR_INTERNAL = 6
 
 DTSORT_OP_U32, DTSORT_OP_U32_KV, DTSORT_OP_U64, DTSORT_OP_U64_KV = 0, 1, 2, 3
-DTSORT_BUCKETING_DIGIT, DTSORT_BUCKETING_LEARNED = 0, 1
+DTSORT_BUCKETING_DIGIT, DTSORT_BUCKETING_LEARNED, DTSORT_BUCKETING_LEARNED_ALWAYS = 0, 1, 2
 
 # C symbols declared in include/dtsort.h
 EXPORTED = [
@@ -88,7 +88,8 @@ class dtsort_stats(ctypes.Structure):
                 ("check_values", ctypes.c_int64 * 2),
                 ("finisher_lsd_tasks", ctypes.c_int64),
                 ("kernel_launches", ctypes.c_int64),
-                ("reserved", ctypes.c_int64 * 3)]
+                ("learned_zones_used", ctypes.c_int64),
+                ("learned_estimate", ctypes.c_double * 2)]
 
     def as_dict(self):
         out = {}

@@ -32,7 +32,7 @@ struct Layout {
   // learned bucketing (lrn_m == 0: digit zones)
   int64_t lrn_m;
   int lrn_B;
-  size_t lsample, lws, lws_bytes, lx, lt, lparams, lpart, lspl, ltab;
+  size_t lsample, lws, lws_bytes, lx, lt, lparams, lpart, lspl, ltab, ldec;
   int64_t maxseg, bmax, hmax, zmax, hashmax, cwords, swords, tmax, mhmax;
   int cap;
   int64_t target;
@@ -149,6 +149,10 @@ Layout make_layout(int kb, int vb, int64_t n, int64_t nsegs, const Opts &o,
 
 constexpr int64_t kLrnMinN = (int64_t)1 << 20;   // smaller arrays use digit zones
 constexpr int kLrnBatch = 8192;
+// extra cost of the learned level 0 over a digit level 0, in distribution
+// passes per record: its histogram and scatter locate each key by the model
+// and the boundaries (measured ~0.5 pass on 10^9 u64 keys)
+constexpr double kLrnPenalty = 0.5;
 
 // Host copy of the device digit-width rule (plan_gamma), for the number of
 // learned zones at level 0.
@@ -219,6 +223,7 @@ void add_learned(Layout &L, int kb, int64_t n, const Opts &o, const KernelShape 
   L.lpart = take(4 * (size_t)(kLrnBatch / 256) * 352);
   L.lspl = take((size_t)kb * 1024);
   L.ltab = take(4 * 1024);
+  L.ldec = take(64);  // decision flag + two estimates
   L.total = off;
 }
 
@@ -347,7 +352,9 @@ dtsort_status run_sort(dtsort_handle h, int op, void *keys, void *vals, const in
   if (ks->blocks_per_sm < 1) return DTSORT_ERR_UNSUPPORTED;
   const Opts o = effective(tuned_options(h, op, n, offsets ? nsegs : 1), *ks);
   Layout L = make_layout(kb, vb, n, offsets ? nsegs : 1, o, *ks);
-  const bool learned = allow_learned && h->opt.bucketing == DTSORT_BUCKETING_LEARNED &&
+  const bool learned = allow_learned &&
+                       (h->opt.bucketing == DTSORT_BUCKETING_LEARNED ||
+                        h->opt.bucketing == DTSORT_BUCKETING_LEARNED_ALWAYS) &&
                        !offsets && n >= kLrnMinN;
   KernelShape *ks64 = nullptr;
   if (learned) {
@@ -417,17 +424,31 @@ dtsort_status run_sort(dtsort_handle h, int op, void *keys, void *vals, const in
                                       w + L.lws, L.lws_bytes, s, false);
     if (st != DTSORT_OK) return st;
     const int steps = h->opt.learned_train_steps > 0 ? h->opt.learned_train_steps : 200;
-    if ((e = dts::lrn_features(smp, L.lrn_m, 8 * kb, x, t, s)) != cudaSuccess ||
-        (e = dts::lrn_init(prm, prm + 352, prm + 704, lseed, s)) != cudaSuccess ||
+    if ((e = dts::lrn_features(smp, L.lrn_m, 8 * kb, x, t, nullptr, s)) != cudaSuccess ||
+        (e = dts::lrn_init(prm, prm + 352, prm + 704, lseed, nullptr, s)) != cudaSuccess ||
         (e = dts::lrn_train(prm, prm + 352, prm + 704, x, t, L.lrn_m, steps, kLrnBatch, 1e-2f,
-                            (float *)(w + L.lpart), s)) != cudaSuccess ||
-        (e = dts::lrn_splitters(prm, L.lrn_B, kb, w + L.lspl, (float *)(w + L.ltab), s)) !=
-            cudaSuccess)
+                            (float *)(w + L.lpart), nullptr, s)) != cudaSuccess ||
+        (e = dts::lrn_splitters(prm, L.lrn_B, kb, w + L.lspl, (float *)(w + L.ltab), nullptr,
+                                s)) != cudaSuccess)
       return DTSORT_ERR_CUDA;
     h->launches += 4 + 2 * (int64_t)steps;  // gather, features, init, training, boundaries
+    // LEARNED: the device decides, from the sorted sample, whether the model's
+    // zones pay (level 0 reads its flag); ALWAYS: they are used
+    const bool decide = h->opt.bucketing == DTSORT_BUCKETING_LEARNED;
+    int *on = decide ? (int *)(w + L.ldec) : nullptr;
+    double *est = decide ? (double *)(w + L.ldec + 8) : nullptr;
+    if (decide) {
+      if ((e = dts::lrn_decide(smp, L.lrn_m, n, kb, L.lrn_B, w + L.lspl, L.cap, L.target,
+                               std::min(o.gamma_max, dts::GAMMA_HW), kLrnPenalty, on, est,
+                               s)) != cudaSuccess)
+        return DTSORT_ERR_CUDA;
+      h->launches += 1;
+    }
     P.lrn_B = L.lrn_B;
     P.lrn_spl = w + L.lspl;
     P.lrn_tab = (const float *)(w + L.ltab);
+    P.lrn_on = on;
+    P.lrn_est = est;
   }
   e = cudaMemsetAsync(P.ctl, 0, sizeof(dts::Ctl), s);
   if (e != cudaSuccess) return DTSORT_ERR_CUDA;
@@ -540,7 +561,8 @@ dtsort_status dtsort_set_options(dtsort_handle h, const dtsort_options *opt) {
   if (!opt) return dtsort_default_options(&h->opt);
   if (opt->gamma_max < 0 || opt->gamma_max > dts::GAMMA_HW || opt->finisher_capacity < 0 ||
       opt->sample_log_factor < 0 || opt->sample_log_factor > 64 ||
-      (opt->bucketing != DTSORT_BUCKETING_DIGIT && opt->bucketing != DTSORT_BUCKETING_LEARNED) ||
+      (opt->bucketing != DTSORT_BUCKETING_DIGIT && opt->bucketing != DTSORT_BUCKETING_LEARNED &&
+       opt->bucketing != DTSORT_BUCKETING_LEARNED_ALWAYS) ||
       opt->learned_segments < 0 || opt->learned_train_steps < 0 || opt->wait_limit_ms < 0 ||
       opt->debug_fault < 0 || opt->debug_fault > 1 || opt->launch_mode < 0 ||
       opt->launch_mode > 2 || opt->block_tiles < 0 || opt->block_tiles > 8)
@@ -567,7 +589,9 @@ dtsort_status dtsort_workspace_bytes(dtsort_handle h, dtsort_op op, int64_t n,
   const Opts o = effective(tuned_options(h, op, n, num_segments > 0 ? num_segments : 1), *ks);
   const int kb = key_bytes(op), vb = has_vals(op) ? kb : 0;
   Layout L = make_layout(kb, vb, n, num_segments > 0 ? num_segments : 1, o, *ks);
-  if (h->opt.bucketing == DTSORT_BUCKETING_LEARNED && n >= kLrnMinN) {
+  if ((h->opt.bucketing == DTSORT_BUCKETING_LEARNED ||
+       h->opt.bucketing == DTSORT_BUCKETING_LEARNED_ALWAYS) &&
+      n >= kLrnMinN) {
     KernelShape *ks64 = nullptr;
     if (get_shape(h, DTSORT_OP_U64, &ks64) != cudaSuccess) return DTSORT_ERR_CUDA;
     add_learned(L, kb, n, o, *ks64);
@@ -656,6 +680,9 @@ dtsort_status dtsort_get_stats(dtsort_handle h, dtsort_stats *out) {
   for (int k = 0; k < 8; ++k) out->phase_ms[k] = d.phase_ms[k];
   out->finisher_lsd_tasks = d.fin_lsd_tasks;
   out->kernel_launches = h->launches;
+  out->learned_zones_used = d.learned_used;
+  out->learned_estimate[0] = d.learned_est[0];
+  out->learned_estimate[1] = d.learned_est[1];
   out->check_site = d.check_site;
   out->check_values[0] = d.check_values[0];
   out->check_values[1] = d.check_values[1];

@@ -135,6 +135,8 @@ struct DevStats {
   double phase_ms[8];
   int64_t check_site, check_values[2];
   int64_t fin_lsd_tasks;
+  int64_t learned_used;
+  double learned_est[2];
 };
 
 struct Params {
@@ -155,6 +157,8 @@ struct Params {
   int32_t lrn_B;          // learned zones at level 0 (0: digit zones)
   const void *lrn_spl;    // lrn_B zone lower bounds (key type), spl[0] = 0
   const float *lrn_tab;   // LRN_TAB_N + 1 predicted CDF values on the feature grid
+  const int *lrn_on;      // NULL, or the device's decision (1: use the learned zones)
+  const double *lrn_est;  // NULL, or the decision's two cost estimates
   unsigned long long wait_ns;  // bound of every spin-wait
   Ctl *ctl;
   Seg *segs[2];
@@ -312,6 +316,12 @@ __device__ __forceinline__ T block_excl_scan(T v, T *sh, T &total) {
   total = sh[NWARP - 1];
   __syncthreads();
   return base + x - v;
+}
+
+// Level 0 uses learned zones: a model was fitted and (when an estimate was
+// made) the estimate chose it.
+__device__ __forceinline__ bool learned_level(const Params &P, int level) {
+  return level == 0 && P.lrn_B > 0 && (P.lrn_on == nullptr || *(volatile const int *)P.lrn_on);
 }
 
 // Digit of a key on the fast path: bits [lo, lo + log2(gmask+1)) of

@@ -44,12 +44,19 @@ DTS_DECLARE_SAMPLE(u64)
 // learned bucketing (dtsort_learned.cu)
 cudaError_t lrn_gather(const void *keys, int kb, int64_t n, uint64_t seed, uint64_t *out,
                        int64_t m, cudaStream_t s);
+// en: NULL, or a device flag (0: the model is not wanted; the kernels return)
 cudaError_t lrn_features(const uint64_t *sorted, int64_t m, int w, float *x, float *t,
-                         cudaStream_t s);
-cudaError_t lrn_init(float *params, float *mom, float *vel, uint64_t seed, cudaStream_t s);
+                         const int *en, cudaStream_t s);
+cudaError_t lrn_init(float *params, float *mom, float *vel, uint64_t seed, const int *en,
+                     cudaStream_t s);
 cudaError_t lrn_train(float *params, float *mom, float *vel, const float *x, const float *t,
-                      int64_t m, int steps, int batch, float lr, float *part, cudaStream_t s);
+                      int64_t m, int steps, int batch, float lr, float *part, const int *en,
+                      cudaStream_t s);
 cudaError_t lrn_splitters(const float *params, int B, int kb, void *spl, float *tab,
-                          cudaStream_t s);
+                          const int *en, cudaStream_t s);
+// the device's decision whether learned zones pay (see lrn_decide_kernel)
+cudaError_t lrn_decide(const uint64_t *sorted, int64_t m, int64_t n, int kb, int B,
+                       const void *spl, int cap, int64_t target, int gmax, double penalty,
+                       int *on, double *est, cudaStream_t s);
 
 }  // namespace dts

@@ -31,7 +31,9 @@ __global__ void lrn_gather_kernel(const K *__restrict__ keys, int64_t n, uint64_
 
 // features of the sorted sample and their empirical CDF targets
 __global__ void lrn_features_kernel(const uint64_t *__restrict__ sorted, int64_t m, int w,
-                                    float *__restrict__ x, float *__restrict__ t) {
+                                    float *__restrict__ x, float *__restrict__ t,
+                                    const int *en) {
+  if (en && !*en) return;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
        i += (int64_t)gridDim.x * blockDim.x) {
     x[i] = mlp_feature(sorted[i], w);
@@ -58,36 +60,50 @@ cudaError_t lrn_gather(const void *keys, int kb, int64_t n, uint64_t seed, uint6
 }
 
 cudaError_t lrn_features(const uint64_t *sorted, int64_t m, int w, float *x, float *t,
-                         cudaStream_t s) {
-  lrn_features_kernel<<<grid_for(m, 256), 256, 0, s>>>(sorted, m, w, x, t);
+                         const int *en, cudaStream_t s) {
+  lrn_features_kernel<<<grid_for(m, 256), 256, 0, s>>>(sorted, m, w, x, t, en);
   return cudaGetLastError();
 }
 
-cudaError_t lrn_init(float *params, float *mom, float *vel, uint64_t seed, cudaStream_t s) {
-  mlp_init_kernel<<<1, 352, 0, s>>>(params, mom, vel, seed);
+cudaError_t lrn_init(float *params, float *mom, float *vel, uint64_t seed, const int *en,
+                     cudaStream_t s) {
+  mlp_init_kernel<<<1, 352, 0, s>>>(params, mom, vel, seed, en);
   return cudaGetLastError();
 }
 
 // `steps` Adam steps on batches of `batch` points strided over the m points
 // (batch s uses points (s mod stride) + i * stride, stride = m / batch).
 cudaError_t lrn_train(float *params, float *mom, float *vel, const float *x, const float *t,
-                      int64_t m, int steps, int batch, float lr, float *part, cudaStream_t s) {
+                      int64_t m, int steps, int batch, float lr, float *part, const int *en,
+                      cudaStream_t s) {
   const int64_t stride = std::max<int64_t>(1, m / batch);
   const int nb = (batch + MLP_BLK - 1) / MLP_BLK;
   for (int k = 1; k <= steps; ++k) {
     mlp_grad_kernel<<<nb, MLP_BLK, 0, s>>>(params, x, t, m, (k - 1) % stride, stride, batch,
-                                           part);
-    mlp_adam_kernel<<<1, 352, 0, s>>>(params, mom, vel, part, nb, batch, nullptr, k, lr);
+                                           part, en);
+    mlp_adam_kernel<<<1, 352, 0, s>>>(params, mom, vel, part, nb, batch, nullptr, k, lr, en);
   }
   return cudaGetLastError();
 }
 
 cudaError_t lrn_splitters(const float *params, int B, int kb, void *spl, float *tab,
-                          cudaStream_t s) {
+                          const int *en, cudaStream_t s) {
   if (kb == 4)
-    lrn_splitters_kernel<uint32_t><<<1, 512, 0, s>>>(params, B, 32, (uint32_t *)spl, tab);
+    lrn_splitters_kernel<uint32_t><<<1, 512, 0, s>>>(params, B, 32, (uint32_t *)spl, tab, en);
   else
-    lrn_splitters_kernel<uint64_t><<<1, 512, 0, s>>>(params, B, 64, (uint64_t *)spl, tab);
+    lrn_splitters_kernel<uint64_t><<<1, 512, 0, s>>>(params, B, 64, (uint64_t *)spl, tab, en);
+  return cudaGetLastError();
+}
+
+cudaError_t lrn_decide(const uint64_t *sorted, int64_t m, int64_t n, int kb, int B,
+                       const void *spl, int cap, int64_t target, int gmax, double penalty,
+                       int *on, double *est, cudaStream_t s) {
+  if (kb == 4)
+    lrn_decide_kernel<uint32_t><<<1, 512, 0, s>>>(sorted, m, n, 32, B, (const uint32_t *)spl,
+                                                  cap, target, gmax, penalty, on, est);
+  else
+    lrn_decide_kernel<uint64_t><<<1, 512, 0, s>>>(sorted, m, n, 64, B, (const uint64_t *)spl,
+                                                  cap, target, gmax, penalty, on, est);
   return cudaGetLastError();
 }
 
@@ -111,9 +127,9 @@ dtsort_status dtsort_mlp_grad(const float *params, const float *x, const float *
     return DTSORT_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   const int nb = (int)((n + dts::MLP_BLK - 1) / dts::MLP_BLK);
-  dts::mlp_grad_kernel<<<nb, dts::MLP_BLK, 0, s>>>(params, x, t, n, 0, 1, n, partial);
+  dts::mlp_grad_kernel<<<nb, dts::MLP_BLK, 0, s>>>(params, x, t, n, 0, 1, n, partial, nullptr);
   dts::mlp_adam_kernel<<<1, 352, 0, s>>>(nullptr, nullptr, nullptr, partial, nb, n, grad_out,
-                                         0, 0.f);
+                                         0, 0.f, nullptr);
   return cudaGetLastError() == cudaSuccess ? DTSORT_OK : DTSORT_ERR_CUDA;
 }
 
@@ -122,7 +138,7 @@ dtsort_status dtsort_mlp_adam(float *params, float *m, float *v, const float *gr
   if (!params || !m || !v || !grad || step < 1) return DTSORT_ERR_INVALID_ARG;
   // a single "partial" equal to the gradient, one block
   dts::mlp_adam_kernel<<<1, 352, 0, (cudaStream_t)stream>>>(params, m, v, grad, 1, 1, nullptr,
-                                                            step, lr);
+                                                            step, lr, nullptr);
   return cudaGetLastError() == cudaSuccess ? DTSORT_OK : DTSORT_ERR_CUDA;
 }
 
@@ -132,7 +148,7 @@ dtsort_status dtsort_mlp_train(float *params, float *m, float *v, const float *x
   if (!params || !m || !v || !x || !t || !partial || n <= 0 || steps < 0 || batch <= 0 ||
       batch > n)
     return DTSORT_ERR_INVALID_ARG;
-  return dts::lrn_train(params, m, v, x, t, n, steps, batch, lr, partial,
+  return dts::lrn_train(params, m, v, x, t, n, steps, batch, lr, partial, nullptr,
                         (cudaStream_t)stream) == cudaSuccess
              ? DTSORT_OK
              : DTSORT_ERR_CUDA;

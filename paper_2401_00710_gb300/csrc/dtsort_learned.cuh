@@ -59,9 +59,13 @@ __global__ void __launch_bounds__(256) mlp_forward_kernel(const float *__restric
 // [b*256, (b+1)*256) of the batch and writes its partial gradient (sums in a
 // fixed order, so the result is deterministic) to part[b][0..321); the loss
 // contribution goes to part[b][321].
+// en: NULL, or a device flag; 0 makes the kernel return at once (the model
+// is not wanted).  The same holds for the other training kernels below.
 __global__ void __launch_bounds__(MLP_BLK) mlp_grad_kernel(
     const float *__restrict__ params, const float *__restrict__ x, const float *__restrict__ t,
-    int64_t m, int64_t first, int64_t stride, int64_t batch, float *__restrict__ part) {
+    int64_t m, int64_t first, int64_t stride, int64_t batch, float *__restrict__ part,
+    const int *en) {
+  if (en && !*en) return;
   __shared__ float p[MLP_NP];
   __shared__ float xs[MLP_BLK], dys[MLP_BLK], es[MLP_BLK];
   __shared__ float h1s[MLP_BLK][MLP_H + 1], h2s[MLP_BLK][MLP_H + 1];
@@ -148,7 +152,8 @@ __global__ void __launch_bounds__(352) mlp_adam_kernel(float *__restrict__ param
                                                        float *__restrict__ vel,
                                                        const float *__restrict__ part, int nb,
                                                        int64_t batch, float *__restrict__ grad,
-                                                       int step, float lr) {
+                                                       int step, float lr, const int *en) {
+  if (en && !*en) return;
   const int i = threadIdx.x;
   if (i > MLP_NP) return;
   float g = 0.f;
@@ -176,7 +181,9 @@ __global__ void __launch_bounds__(352) mlp_adam_kernel(float *__restrict__ param
 template <typename K>
 __global__ void __launch_bounds__(512) lrn_splitters_kernel(const float *__restrict__ params,
                                                             int B, int w, K *__restrict__ spl,
-                                                            float *__restrict__ tab) {
+                                                            float *__restrict__ tab,
+                                                            const int *en) {
+  if (en && !*en) return;
   __shared__ float p[MLP_NP];
   __shared__ float ts[LRN_TAB + 1];
   __shared__ K ss[1024];
@@ -223,7 +230,8 @@ __global__ void __launch_bounds__(512) lrn_splitters_kernel(const float *__restr
 // Deterministic parameter initialisation from a seed: uniform in
 // [-a, a] per layer (a = sqrt(6 / (fan_in + fan_out))), biases 0.
 __global__ void mlp_init_kernel(float *__restrict__ params, float *__restrict__ mom,
-                                float *__restrict__ vel, uint64_t seed) {
+                                float *__restrict__ vel, uint64_t seed, const int *en) {
+  if (en && !*en) return;
   const int i = threadIdx.x + blockIdx.x * blockDim.x;
   if (i >= MLP_NP) return;
   uint64_t z = seed + (uint64_t)(i + 1) * 0x9E3779B97F4A7C15ull;
@@ -238,6 +246,76 @@ __global__ void mlp_init_kernel(float *__restrict__ params, float *__restrict__ 
   params[i] = (2.f * u - 1.f) * a;
   mom[i] = 0.f;
   vel[i] = 0.f;
+}
+
+// Distribution levels below a subproblem of s records under the digit-width
+// rule (the fewest levels of at most gmax bits that bring buckets to target),
+// none when it fits the base case.
+__device__ __forceinline__ int levels_below(double s, double cap, double target, int gmax) {
+  if (s <= cap) return 0;
+  int e = 0;
+  while (e < 62 && target * (double)(1ull << e) < s) ++e;
+  return (e + gmax - 1) / gmax;
+}
+
+// Whether learned level-0 zones pay, from the sorted model sample (m keys of
+// the n): the record-passes below level 0 with the digit zones against those
+// with the model's zones [spl[z], spl[z+1]) plus the learned level's extra
+// cost of `penalty` record-passes per record; each zone's size is estimated
+// from the sample and costs the levels it needs.  One CTA; writes the
+// decision and both estimates (per record).
+template <typename K>
+__global__ void __launch_bounds__(512) lrn_decide_kernel(
+    const uint64_t *__restrict__ sorted, int64_t m, int64_t n, int key_bits, int B,
+    const K *__restrict__ spl, int cap, int64_t target, int gmax, double penalty, int *on,
+    double *est) {
+  __shared__ double red[2][32];
+  const uint64_t mask = key_bits >= 64 ? ~0ull : ((1ull << key_bits) - 1ull);
+  const uint64_t rmax = sorted[m - 1] & mask;
+  const int t = rmax ? 64 - __clzll((long long)rmax) : 0;
+  const int g = 31 - __clz(B);
+  const int lo = t - g > 0 ? t - g : 0;
+  const int nz = 1 << (t - lo);
+  auto lower_bound = [&](uint64_t v) -> int64_t {  // first index with sorted[i] >= v
+    int64_t a = 0, b = m;
+    while (a < b) {
+      const int64_t mid = (a + b) >> 1;
+      if (sorted[mid] < v) a = mid + 1;
+      else b = mid;
+    }
+    return a;
+  };
+  auto cost = [&](int64_t c0, int64_t c1) {
+    const double s = (double)(c1 - c0) * (double)n / (double)m;
+    return s * (double)levels_below(s, (double)cap, (double)target, gmax);
+  };
+  double ad = 0.0, al = 0.0;
+  for (int z = threadIdx.x; z < nz; z += blockDim.x)
+    ad += cost(lower_bound((uint64_t)z << lo),
+               z + 1 < nz ? lower_bound((uint64_t)(z + 1) << lo) : m);
+  for (int z = threadIdx.x; z < B; z += blockDim.x)
+    al += cost(z ? lower_bound((uint64_t)spl[z]) : 0,
+               z + 1 < B ? lower_bound((uint64_t)spl[z + 1]) : m);
+  for (int o = 16; o > 0; o >>= 1) {
+    ad += __shfl_xor_sync(0xffffffffu, ad, o);
+    al += __shfl_xor_sync(0xffffffffu, al, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = ad;
+    red[1][threadIdx.x >> 5] = al;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double cd = 0.0, cl = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
+      cd += red[0][i];
+      cl += red[1][i];
+    }
+    cl += penalty * (double)n;
+    *on = cd > cl ? 1 : 0;
+    est[0] = cd / (double)n;
+    est[1] = cl / (double)n;
+  }
 }
 
 }  // namespace dts

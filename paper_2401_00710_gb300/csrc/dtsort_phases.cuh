@@ -201,7 +201,7 @@ __device__ void phase_setup(const Params &P, int level, unsigned char *smem) {
       const Seg s = ldcg_obj(&P.segs[p][i]);
       sz = s.size;
       g = plan_gamma(s.size, P.target, P.gamma_max, s.hi, FIN_DIG);
-      if (level == 0 && P.lrn_B > 0) g = 31 - __clz(P.lrn_B);  // learned zones
+      if (learned_level(P, level)) g = 31 - __clz(P.lrn_B);  // learned zones
       const int64_t blk = (int64_t)P.blk_tiles * S::TILE;
       nblk = (s.size + blk - 1) / blk;
       nchk = (nblk + S::CH - 1) / S::CH;
@@ -286,7 +286,7 @@ __device__ void phase_sample(const Params &P, int level, unsigned char *smem) {
     const int g = I.gamma;
     const int hcap = (1 << (g - 1)) < HEAVY_HW ? (1 << (g - 1)) : HEAVY_HW;
     const int64_t nbm = (1 << g) + hcap + 1;
-    const bool learned = level == 0 && P.lrn_B > 0;
+    const bool learned = learned_level(P, level);
     for (int64_t b = threadIdx.x; b < nbm; b += NT) P.bcount[I.boff + b] = 0;
     int L = 0;
     while (L < 63 && (1ll << L) < S.ntotal) ++L;
@@ -1389,6 +1389,9 @@ __device__ __forceinline__ void write_stats(const Params &P, unsigned long long 
     d->learned_cv = mean > 0 ? sqrt(var > 0 ? var : 0.0) / mean : 0.0;
     d->learned_mom = mean > 0 ? (double)ld_cg64(&c->st_bmax) / mean : 0.0;
     d->fin_lsd_tasks = ld_cg64(&c->st_fin_lsd_tasks);
+    d->learned_used = learned_level(P, 0) ? 1 : 0;
+    d->learned_est[0] = P.lrn_est ? P.lrn_est[0] : 0.0;
+    d->learned_est[1] = P.lrn_est ? P.lrn_est[1] : 0.0;
     d->check_site = ld_cg64(&c->dbg[0]);
     d->check_values[0] = ld_cg64(&c->dbg[1]);
     d->check_values[1] = ld_cg64(&c->dbg[2]);

@@ -139,12 +139,12 @@ def test_learned_sort_matches_oracle(G, name, dtype):
     n = 2_000_003
     keys = gen.family(name, n, dtype, seed=12)
     vals = gen.iota(n, dtype)
-    G.set_options(bucketing=dts.DTSORT_BUCKETING_LEARNED, learned_train_steps=100)
+    G.set_options(bucketing=dts.DTSORT_BUCKETING_LEARNED_ALWAYS, learned_train_steps=100)
     gk, gv = G.sort(keys, vals)
     ek, ev = oracle.stable_sort(keys, vals)
     gpu_util.assert_same(gk, gv, ek, ev)
     st = G.stats()
-    assert st["status"] == 0
+    assert st["status"] == 0 and st["learned_zones_used"] == 1
     G.reset_options()
 
 
@@ -158,7 +158,7 @@ def test_learned_zones_balance_the_skewed_mixture(G):
     G.set_options(bucketing=dts.DTSORT_BUCKETING_DIGIT)
     G.sort(keys, vals)
     digit = G.stats()
-    G.set_options(bucketing=dts.DTSORT_BUCKETING_LEARNED)
+    G.set_options(bucketing=dts.DTSORT_BUCKETING_LEARNED_ALWAYS)
     gk, gv = G.sort(keys, vals)
     lrn = G.stats()
     G.reset_options()
@@ -168,3 +168,28 @@ def test_learned_zones_balance_the_skewed_mixture(G):
     assert lrn["learned_bucket_max_over_mean"] < digit["learned_bucket_max_over_mean"]
     # most keys need no fix-up step beyond the model's prediction
     assert lrn["learned_fixup_records"] < 0.5 * n
+
+
+def test_learned_bucketing_is_used_only_when_it_pays(G):
+    # bucketing LEARNED estimates, from the sorted model sample, the
+    # distribution passes below level 0 with digit zones and with the model's
+    # zones (+ their extra cost) and keeps the cheaper.  Uniform keys: every
+    # digit zone already needs the fewest levels, so the digit zones stay.
+    # Bit-exponential keys (roughly log-uniform; most fall into the lowest
+    # top-bit zone): whichever the estimate picks, the output is the oracle's
+    n = 8_000_000
+    G.set_options(bucketing=dts.DTSORT_BUCKETING_LEARNED, learned_train_steps=60)
+    used = {}
+    for name in ("uniform", "bitexp"):
+        keys = gen.family(name, n, np.uint64, seed=31)
+        vals = gen.iota(n, np.uint64)
+        gk, gv = G.sort(keys, vals)
+        ek, ev = oracle.stable_sort(keys, vals)
+        gpu_util.assert_same(gk, gv, ek, ev)
+        st = G.stats()
+        digit_cost, learned_cost = st["learned_estimate"]
+        assert digit_cost > 0 and learned_cost > 0
+        assert st["learned_zones_used"] == (1 if digit_cost > learned_cost else 0)
+        used[name] = (st["learned_zones_used"], digit_cost, learned_cost)
+    G.reset_options()
+    assert used["uniform"][0] == 0, used
