@@ -348,21 +348,25 @@ def run_ours(args):
     # ---- end to end: host buffers in, sorted host buffers out ----
     e2e = None
     if not args.no_e2e:
-        ok_k = torch.empty_like(hk, pin_memory=True)
-        ok_v = torch.empty_like(hv, pin_memory=True) if has_v else None
+        # through the host-buffer entry point: it copies the pinned host arrays
+        # in, sorts, and copies the result back over them; the pristine input
+        # is restored on the host between steps (untimed)
+        wk = torch.empty_like(hk, pin_memory=True)
+        wv = torch.empty_like(hv, pin_memory=True) if has_v else None
         e_ms = []
         for i in range(max(1, min(args.steps, 3))):
+            wk.copy_(hk)
+            if has_v:
+                wv.copy_(hv)
             barrier()
             t0 = torch.cuda.Event(enable_timing=True)
             t1 = torch.cuda.Event(enable_timing=True)
             t0.record(stream)
-            k.copy_(hk, non_blocking=True)
-            if has_v:
-                v.copy_(hv, non_blocking=True)
-            sort_once(k.data_ptr(), v.data_ptr() if has_v else None)
-            ok_k.copy_(k, non_blocking=True)
-            if has_v:
-                ok_v.copy_(v, non_blocking=True)
+            st = dts.dtsort_sort_host(h, op, wk.data_ptr(), wv.data_ptr() if has_v else None, n,
+                                      k.data_ptr(), v.data_ptr() if has_v else None,
+                                      ws.data_ptr(), wsb, sp)
+            if st != 0:
+                raise RuntimeError(dts.status_string(st))
             t1.record(stream)
             barrier()
             e_ms.append(t0.elapsed_time(t1))

@@ -201,6 +201,22 @@ DTSORT_API dtsort_status dtsort_u64_kv(dtsort_handle h, uint64_t *keys, uint64_t
                             int64_t n, void *workspace, size_t workspace_bytes,
                             dtsort_stream stream);
 
+/* The same sort for records in HOST memory (Sec. 2's problem on host
+ * buffers): copies the n keys (and values, if op has values) from keys_host /
+ * values_host into the caller's DEVICE buffers dev_keys / dev_values, sorts
+ * them there exactly as dtsort_u32 ... dtsort_u64_kv, and copies the result
+ * back over the host arrays.  All three steps are enqueued on `stream`; the
+ * host arrays hold the result once the stream has reached this point (host
+ * memory should be pinned, e.g. cudaHostAlloc, for the copies to be
+ * asynchronous; pageable memory works but the copies then synchronise).
+ * values_host / dev_values must be NULL for a key-only op.  No allocation.
+ * Errors: as the device entry points; DTSORT_ERR_CUDA if a copy cannot be
+ * enqueued.  (The paper has no counterpart: it sorts in host memory.) */
+DTSORT_API dtsort_status dtsort_sort_host(dtsort_handle h, dtsort_op op, void *keys_host,
+                              void *values_host, int64_t n, void *dev_keys,
+                              void *dev_values, void *workspace,
+                              size_t workspace_bytes, dtsort_stream stream);
+
 /* Segmented (batched) stable sort: every array s = [offsets[s], offsets[s+1])
  * of keys/values is sorted on its own, all in one persistent kernel launch.
  * offsets: DEVICE int64[num_segments + 1], offsets[0] == 0, non-decreasing,

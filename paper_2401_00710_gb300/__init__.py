@@ -31,7 +31,7 @@ EXPORTED = [
     "dtsort_status_string", "dtsort_create", "dtsort_destroy",
     "dtsort_default_options", "dtsort_set_options", "dtsort_get_options",
     "dtsort_workspace_bytes", "dtsort_u32", "dtsort_u32_kv", "dtsort_u64",
-    "dtsort_u64_kv", "dtsort_segmented_u32", "dtsort_segmented_u32_kv",
+    "dtsort_u64_kv", "dtsort_sort_host", "dtsort_segmented_u32", "dtsort_segmented_u32_kv",
     "dtsort_segmented_u64", "dtsort_segmented_u64_kv",
     "dtsort_last_device_error", "dtsort_get_stats", "dtsort_debug_sample",
     "dtsort_u32_kv_noalloc", "dtsort_autotune", "dtsort_autotune_scratch_bytes",
@@ -151,6 +151,7 @@ def _declare(L):
         getattr(L, name).argtypes = [_H, _P, _P, _I64, _I64, _P, _SZ, _P]
     for name in ("dtsort_segmented_u32_kv", "dtsort_segmented_u64_kv"):
         getattr(L, name).argtypes = [_H, _P, _P, _P, _I64, _I64, _P, _SZ, _P]
+    L.dtsort_sort_host.argtypes = [_H, ctypes.c_int, _P, _P, _I64, _P, _P, _P, _SZ, _P]
     L.dtsort_last_device_error.argtypes = [_H, _P]
     L.dtsort_get_stats.argtypes = [_H, ctypes.POINTER(dtsort_stats)]
     L.dtsort_debug_sample.argtypes = [_H, _P, ctypes.c_int, _I64, _I64,
@@ -234,6 +235,12 @@ def dtsort_u64(h, keys, n, ws, ws_bytes, stream=0):
 
 def dtsort_u64_kv(h, keys, values, n, ws, ws_bytes, stream=0):
     return lib().dtsort_u64_kv(h, keys, values, n, ws, ws_bytes, stream or None)
+
+
+def dtsort_sort_host(h, op, keys_host, values_host, n, dev_keys, dev_values, ws, ws_bytes,
+                     stream=0):
+    return lib().dtsort_sort_host(h, op, keys_host, values_host, n, dev_keys, dev_values, ws,
+                                  ws_bytes, stream or None)
 
 
 def dtsort_segmented_u32(h, keys, offsets, num_segments, n, ws, ws_bytes, stream=0):

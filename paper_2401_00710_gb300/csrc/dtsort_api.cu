@@ -642,6 +642,31 @@ dtsort_status dtsort_segmented_u64_kv(dtsort_handle h, uint64_t *keys, uint64_t 
   return run_sort(h, DTSORT_OP_U64_KV, keys, values, off, ns, n, ws, wsb, (cudaStream_t)s);
 }
 
+dtsort_status dtsort_sort_host(dtsort_handle h, dtsort_op op, void *keys_host, void *values_host,
+                               int64_t n, void *dev_keys, void *dev_values, void *ws, size_t wsb,
+                               dtsort_stream stream) {
+  if (!h || op < 0 || op >= kOps || n < 0) return DTSORT_ERR_INVALID_ARG;
+  if (n == 0) return DTSORT_OK;
+  const bool hv = has_vals(op);
+  if (!keys_host || !dev_keys || (hv && (!values_host || !dev_values)) ||
+      (!hv && (values_host || dev_values)))
+    return DTSORT_ERR_INVALID_ARG;
+  const size_t bytes = (size_t)n * key_bytes(op);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (cudaMemcpyAsync(dev_keys, keys_host, bytes, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      (hv && cudaMemcpyAsync(dev_values, values_host, bytes, cudaMemcpyHostToDevice, s) !=
+                 cudaSuccess))
+    return DTSORT_ERR_CUDA;
+  const dtsort_status st =
+      run_sort(h, op, dev_keys, hv ? dev_values : nullptr, nullptr, 1, n, ws, wsb, s);
+  if (st != DTSORT_OK) return st;
+  if (cudaMemcpyAsync(keys_host, dev_keys, bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      (hv && cudaMemcpyAsync(values_host, dev_values, bytes, cudaMemcpyDeviceToHost, s) !=
+                 cudaSuccess))
+    return DTSORT_ERR_CUDA;
+  return DTSORT_OK;
+}
+
 dtsort_status dtsort_last_device_error(dtsort_handle h, dtsort_stream s) {
   if (!h) return DTSORT_ERR_INVALID_ARG;
   if (cudaStreamSynchronize((cudaStream_t)s) != cudaSuccess) return DTSORT_ERR_CUDA;

@@ -350,3 +350,37 @@ def test_bounded_wait_expires_without_hanging(G):
     assert G.device_status() == dts.DTSORT_ERR_DEVICE_TIMEOUT
     G.reset_options()
     check(G, keys, vals)
+
+
+@pytest.mark.parametrize("dtype,kv", [(np.uint32, True), (np.uint64, True), (np.uint32, False)])
+def test_sort_from_host_buffers(G, dtype, kv):
+    # dtsort_sort_host: pinned host arrays in, sorted host arrays out, through
+    # the caller's device buffers and workspace
+    n = 1_234_567
+    keys = gen.family("zipf1.2hash" if dtype == np.uint64 else "zipf1.0", n, dtype, seed=41)
+    vals = gen.iota(n, dtype) if kv else None
+    tdt = torch.int32 if dtype == np.uint32 else torch.int64
+    hk = torch.from_numpy(keys.view(np.int32 if dtype == np.uint32 else np.int64)).pin_memory()
+    hv = (torch.from_numpy(vals.view(np.int32 if dtype == np.uint32 else np.int64)).pin_memory()
+          if kv else None)
+    dk = torch.empty(n, dtype=tdt, device=G.dev)
+    dv = torch.empty(n, dtype=tdt, device=G.dev) if kv else None
+    op = gpu_util.op_of(keys, vals)
+    ws = G.workspace(op, n)
+    s = torch.cuda.current_stream(G.dev).cuda_stream
+    st = dts.dtsort_sort_host(G.h, op, hk.data_ptr(), hv.data_ptr() if kv else None, n,
+                              dk.data_ptr(), dv.data_ptr() if kv else None, ws.data_ptr(),
+                              ws.numel(), s)
+    assert st == dts.DTSORT_OK
+    torch.cuda.synchronize()
+    assert G.device_status() == dts.DTSORT_OK
+    ek, ev = oracle.stable_sort(keys, vals)
+    gk = hk.numpy().view(dtype)
+    gv = hv.numpy().view(dtype) if kv else None
+    gpu_util.assert_same(gk, gv, ek, ev)
+    # a key-only op must not be given values, a key/value op must be
+    bad_op = dts.DTSORT_OP_U32 if dtype == np.uint32 else dts.DTSORT_OP_U64
+    if kv:
+        assert dts.dtsort_sort_host(G.h, bad_op, hk.data_ptr(), hv.data_ptr(), n, dk.data_ptr(),
+                                    dv.data_ptr(), ws.data_ptr(), ws.numel(),
+                                    s) == dts.DTSORT_ERR_INVALID_ARG
