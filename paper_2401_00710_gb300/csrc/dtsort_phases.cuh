@@ -1315,14 +1315,22 @@ __device__ void phase_merge(const Params &P, int level, unsigned char *smem) {
     K *vout = HV ? (K *)P.vals[Z.obuf] : nullptr;
     const int64_t o0 = Z.zs + (ch - Z.chunk0) * MERGE_CHUNK;
     const int64_t o1 = o0 + MERGE_CHUNK < Z.ze ? o0 + MERGE_CHUNK : Z.ze;
-    for (int64_t pp = o0 + threadIdx.x; pp < o1; pp += NT) {
-      int lo = 0, hi = Z.m;  // count of heavy buckets starting at or before pp
+    // cnt = heavy buckets starting at or before pp: one binary search for a
+    // thread's first position, then (positions rise by NT) a forward walk
+    int cnt = 0;
+    {
+      int lo = 0, hi = Z.m;
+      const int64_t p0 = o0 + threadIdx.x;
       while (lo < hi) {
         const int mid = (lo + hi) >> 1;
-        if (hs[mid] <= pp) lo = mid + 1;
+        if (hs[mid] <= p0) lo = mid + 1;
         else hi = mid;
       }
-      const int i = lo - 1;
+      cnt = lo;
+    }
+    for (int64_t pp = o0 + threadIdx.x; pp < o1; pp += NT) {
+      while (cnt < Z.m && hs[cnt] <= pp) ++cnt;
+      const int i = cnt - 1;
       int64_t from;
       if (i >= 0 && pp < hs[i] + hz[i]) {
         from = Z.zs + Z.b0 + hp[i] + (pp - hs[i]);
