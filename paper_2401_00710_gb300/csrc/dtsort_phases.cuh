@@ -1328,22 +1328,45 @@ __device__ void phase_merge(const Params &P, int level, unsigned char *smem) {
       }
       cnt = lo;
     }
-    for (int64_t pp = o0 + threadIdx.x; pp < o1; pp += NT) {
-      while (cnt < Z.m && hs[cnt] <= pp) ++cnt;
-      const int i = cnt - 1;
-      int64_t from;
-      if (i >= 0 && pp < hs[i] + hz[i]) {
-        from = Z.zs + Z.b0 + hp[i] + (pp - hs[i]);
-      } else {
-        const int64_t before = i >= 0 ? hp[i] + hz[i] : 0;
-        from = pp - before;
+    // MB positions per thread at a time: their sources first, then all
+    // their loads, then the stores (the loads overlap)
+    constexpr int MB = 8;
+    for (int64_t pb = o0 + threadIdx.x; pb < o1; pb += (int64_t)MB * NT) {
+      int64_t from[MB];
+#pragma unroll
+      for (int r = 0; r < MB; ++r) {
+        const int64_t pp = pb + (int64_t)r * NT;
+        from[r] = -1;
+        if (pp < o1) {
+          while (cnt < Z.m && hs[cnt] <= pp) ++cnt;
+          const int i = cnt - 1;
+          int64_t f;
+          if (i >= 0 && pp < hs[i] + hz[i]) {
+            f = Z.zs + Z.b0 + hp[i] + (pp - hs[i]);
+          } else {
+            const int64_t before = i >= 0 ? hp[i] + hz[i] : 0;
+            f = pp - before;
+          }
+          if (f >= Z.zs && f < Z.ze) from[r] = f;
+          else latch(P, ERR_INTERNAL);
+        }
       }
-      if (from < Z.zs || from >= Z.ze) {
-        latch(P, ERR_INTERNAL);
-        continue;
+      K kk[MB], vv[HV ? MB : 1];
+#pragma unroll
+      for (int r = 0; r < MB; ++r) {
+        if (from[r] >= 0) {
+          kk[r] = ld_key<K>(kin + from[r]);
+          if constexpr (HV) vv[r] = ld_key<K>(vin + from[r]);
+        }
       }
-      kout[pp] = ld_key<K>(kin + from);
-      if constexpr (HV) vout[pp] = ld_key<K>(vin + from);
+#pragma unroll
+      for (int r = 0; r < MB; ++r) {
+        if (from[r] >= 0) {
+          const int64_t pp = pb + (int64_t)r * NT;
+          kout[pp] = kk[r];
+          if constexpr (HV) vout[pp] = vv[r];
+        }
+      }
     }
     my += o1 - o0;
   }
