@@ -982,9 +982,27 @@ __device__ void phase_finish(const Params &P, int level, unsigned char *smem) {
     const K *vsrc = HV ? (const K *)P.vals[tk.src] : nullptr;
     K *vdst = HV ? (K *)P.vals[tk.dst] : nullptr;
     if (tk.kind == TASK_COPY) {
-      for (int64_t i = threadIdx.x; i < tk.size; i += NT) {
-        kdst[tk.start + i] = ld_key<K>(ksrc + tk.start + i);
-        if constexpr (HV) vdst[tk.start + i] = ld_key<K>(vsrc + tk.start + i);
+      // several records per thread at a time: all loads, then all stores
+      // (8 of 32-bit keys, 4 of 64-bit keys: the registers stay within bounds)
+      constexpr int CB = sizeof(K) == 4 ? 8 : 4;
+      for (int64_t i0 = threadIdx.x; i0 < tk.size; i0 += (int64_t)CB * NT) {
+        K kk[CB], vv[HV ? CB : 1];
+#pragma unroll
+        for (int r = 0; r < CB; ++r) {
+          const int64_t i = i0 + (int64_t)r * NT;
+          if (i < tk.size) {
+            kk[r] = ld_key<K>(ksrc + tk.start + i);
+            if constexpr (HV) vv[r] = ld_key<K>(vsrc + tk.start + i);
+          }
+        }
+#pragma unroll
+        for (int r = 0; r < CB; ++r) {
+          const int64_t i = i0 + (int64_t)r * NT;
+          if (i < tk.size) {
+            kdst[tk.start + i] = kk[r];
+            if constexpr (HV) vdst[tk.start + i] = vv[r];
+          }
+        }
       }
       my_copy += tk.size;
       continue;
