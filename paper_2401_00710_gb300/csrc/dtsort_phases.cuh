@@ -297,12 +297,24 @@ __device__ void phase_sample(const Params &P, int level, unsigned char *smem) {
     while (M < m) M <<= 1;
     const uint64_t st = P.seed ^ (uint64_t)S.start ^ ((uint64_t)S.size * 0x9E3779B97F4A7C15ull) ^
                         ((uint64_t)S.hi << 57);
-    for (int k = threadIdx.x; k < M; k += NT) {
-      if (k < m) {
-        const int64_t pos = S.start + (int64_t)(sm64_at(st, (uint64_t)k) % (uint64_t)S.size);
-        Ssm[k] = ld_key<K>(src + pos);
-      } else {
-        Ssm[k] = (K)~(K)0;
+    {
+      // SMAX / NT draws per thread: all positions and loads first, then the
+      // stores (the random loads overlap)
+      constexpr int SB = SMAX / NT;
+      K v[SB];
+#pragma unroll
+      for (int r = 0; r < SB; ++r) {
+        const int k = threadIdx.x + r * NT;
+        v[r] = (K)~(K)0;
+        if (k < m) {
+          const int64_t pos = S.start + (int64_t)(sm64_at(st, (uint64_t)k) % (uint64_t)S.size);
+          v[r] = ld_key<K>(src + pos);
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < SB; ++r) {
+        const int k = threadIdx.x + r * NT;
+        if (k < M) Ssm[k] = v[r];
       }
     }
     __syncthreads();
@@ -982,27 +994,9 @@ __device__ void phase_finish(const Params &P, int level, unsigned char *smem) {
     const K *vsrc = HV ? (const K *)P.vals[tk.src] : nullptr;
     K *vdst = HV ? (K *)P.vals[tk.dst] : nullptr;
     if (tk.kind == TASK_COPY) {
-      // several records per thread at a time: all loads, then all stores
-      // (8 of 32-bit keys, 4 of 64-bit keys: the registers stay within bounds)
-      constexpr int CB = sizeof(K) == 4 ? 8 : 4;
-      for (int64_t i0 = threadIdx.x; i0 < tk.size; i0 += (int64_t)CB * NT) {
-        K kk[CB], vv[HV ? CB : 1];
-#pragma unroll
-        for (int r = 0; r < CB; ++r) {
-          const int64_t i = i0 + (int64_t)r * NT;
-          if (i < tk.size) {
-            kk[r] = ld_key<K>(ksrc + tk.start + i);
-            if constexpr (HV) vv[r] = ld_key<K>(vsrc + tk.start + i);
-          }
-        }
-#pragma unroll
-        for (int r = 0; r < CB; ++r) {
-          const int64_t i = i0 + (int64_t)r * NT;
-          if (i < tk.size) {
-            kdst[tk.start + i] = kk[r];
-            if constexpr (HV) vdst[tk.start + i] = vv[r];
-          }
-        }
+      for (int64_t i = threadIdx.x; i < tk.size; i += NT) {
+        kdst[tk.start + i] = ld_key<K>(ksrc + tk.start + i);
+        if constexpr (HV) vdst[tk.start + i] = ld_key<K>(vsrc + tk.start + i);
       }
       my_copy += tk.size;
       continue;
