@@ -15,11 +15,22 @@ cudaError_t DTS_CAT(shape_, DTS_NAME)(KernelShape *out) {
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
-  // the per-phase kernel too, here and not at launch (launches may be
+  // the per-phase kernels too, here and not at launch (launches may be
   // captured into a graph)
-  e = cudaFuncSetAttribute(dtsort_phase_kernel<DTS_K, DTS_HV>,
-                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
+  const void *pk[] = {
+      (const void *)dtsort_phase_kernel<DTS_K, DTS_HV>,
+      (const void *)dtsort_phase_one<DTS_K, DTS_HV, KP_SEED>,
+      (const void *)dtsort_phase_one<DTS_K, DTS_HV, KP_SETUP>,
+      (const void *)dtsort_phase_one<DTS_K, DTS_HV, KP_SAMPLE>,
+      (const void *)dtsort_phase_one<DTS_K, DTS_HV, KP_HIST>,
+      (const void *)dtsort_phase_one<DTS_K, DTS_HV, KP_MSCAN>,
+      (const void *)dtsort_phase_one<DTS_K, DTS_HV, KP_SCAN>,
+      (const void *)dtsort_phase_one<DTS_K, DTS_HV, KP_SCATTER>,
+      (const void *)dtsort_phase_one<DTS_K, DTS_HV, KP_FINISH>};
+  for (const void *f : pk) {
+    e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
   int nb = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, NT, smem);
   if (e != cudaSuccess) return e;
@@ -40,9 +51,18 @@ cudaError_t DTS_CAT(launch_, DTS_NAME)(const Params &P, int grid, int head, cuda
   const size_t smem = smem_bytes<DTS_K, DTS_HV>();
   cudaError_t e;
   if (head > 0) {
-    auto *pf = dtsort_phase_kernel<DTS_K, DTS_HV>;  // attributes set by shape_
+    // one kernel per phase (attributes set by shape_)
     auto run = [&](int phase, int level, int g, int prev) {
-      pf<<<g, NT, smem, s>>>(P, phase, level, 1, prev);
+      switch (phase) {
+        case KP_SEED: dtsort_phase_one<DTS_K, DTS_HV, KP_SEED><<<g, NT, smem, s>>>(P, level, prev); break;
+        case KP_SETUP: dtsort_phase_one<DTS_K, DTS_HV, KP_SETUP><<<g, NT, smem, s>>>(P, level, prev); break;
+        case KP_SAMPLE: dtsort_phase_one<DTS_K, DTS_HV, KP_SAMPLE><<<g, NT, smem, s>>>(P, level, prev); break;
+        case KP_HIST: dtsort_phase_one<DTS_K, DTS_HV, KP_HIST><<<g, NT, smem, s>>>(P, level, prev); break;
+        case KP_MSCAN: dtsort_phase_one<DTS_K, DTS_HV, KP_MSCAN><<<g, NT, smem, s>>>(P, level, prev); break;
+        case KP_SCAN: dtsort_phase_one<DTS_K, DTS_HV, KP_SCAN><<<g, NT, smem, s>>>(P, level, prev); break;
+        case KP_SCATTER: dtsort_phase_one<DTS_K, DTS_HV, KP_SCATTER><<<g, NT, smem, s>>>(P, level, prev); break;
+        default: dtsort_phase_one<DTS_K, DTS_HV, KP_FINISH><<<g, NT, smem, s>>>(P, level, prev); break;
+      }
       return cudaGetLastError();
     };
     if ((e = run(KP_SEED, 0, grid, -1)) != cudaSuccess) return e;

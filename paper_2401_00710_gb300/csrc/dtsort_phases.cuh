@@ -1594,6 +1594,39 @@ __global__ void __launch_bounds__(NT, 2) dtsort_phase_kernel(const __grid_consta
     c->levels_done = level + 1;
 }
 
+// One phase of a queued level as its own kernel, so that each phase gets a
+// register allocation of its own (the same phases inside one kernel share
+// one, and a change to one phase moved the others').  Launched without the
+// host reading the control block: a phase of a level without subproblems,
+// or any phase after an error, returns at once; the base case of a level
+// records that the level is done.  prev_kind >= 0: the phase-time bucket the
+// time since the previous launch's start goes to.
+template <typename K, bool HV, int PH>
+__global__ void __launch_bounds__(NT, 2) dtsort_phase_one(const __grid_constant__ Params P,
+                                                          int level, int prev_kind) {
+  Ctl *c = P.ctl;
+  if (*(volatile int *)&c->error) return;
+  if (PH >= KP_SETUP && PH <= KP_FINISH && level > 0 && ld_cg64(&c->nseg[level & 1]) == 0)
+    return;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (PH == KP_SEED) c->t_last = c->t_begin = gtimer();
+    else if (prev_kind >= 0) tick(P, prev_kind);
+  }
+  unsigned char *smem = dts_smem;
+  if constexpr (PH == KP_SEED) phase_seed<K, HV>(P);
+  else if constexpr (PH == KP_SETUP) {
+    if (blockIdx.x == 0) phase_setup<K, HV>(P, level, smem);
+  } else if constexpr (PH == KP_SAMPLE) phase_sample<K, HV>(P, level, smem);
+  else if constexpr (PH == KP_HIST) phase_hist<K, HV>(P, level, smem);
+  else if constexpr (PH == KP_MSCAN) phase_mscan<K, HV>(P, level, smem);
+  else if constexpr (PH == KP_SCAN) phase_scan<K, HV>(P, level, smem);
+  else if constexpr (PH == KP_SCATTER) phase_scatter<K, HV>(P, level, smem);
+  else if constexpr (PH == KP_FINISH) {
+    phase_finish<K, HV>(P, level, smem);
+    if (blockIdx.x == 0 && threadIdx.x == 0) c->levels_done = level + 1;
+  }
+}
+
 // ---------------------------------------------------- sampler diagnostic
 // Alg. 2 step 1 on one subproblem, exactly as phase_sample draws it.
 template <typename K>
