@@ -56,6 +56,12 @@ def parse():
                     help="segmented: capture the call once, replay it per step")
     ap.add_argument("--baseline-calls", action="store_true",
                     help="segmented: also time one dtsort_u32_kv call per array")
+    ap.add_argument("--block-tiles", type=int, default=0,
+                    help="option block_tiles (0: the library's default)")
+    ap.add_argument("--gamma-max", type=int, default=0,
+                    help="option gamma_max (0: the library's default)")
+    ap.add_argument("--capacity", type=int, default=0,
+                    help="option finisher_capacity (0: the library's default)")
     ap.add_argument("--bucketing", default="digit",
                     choices=["digit", "learned", "learned-always"],
                     help="learned: model zones when the device's estimate says they pay; "
@@ -289,9 +295,13 @@ def run_ours(args):
     op = {"u32kv": dts.DTSORT_OP_U32_KV, "u32": dts.DTSORT_OP_U32,
           "u64kv": dts.DTSORT_OP_U64_KV, "u64": dts.DTSORT_OP_U64}[args.op]
     h = dts.dtsort_create(local)
-    if args.launch_mode or args.bucketing != "digit":
+    if (args.launch_mode or args.bucketing != "digit" or args.block_tiles or args.gamma_max or
+            args.capacity):
         o = dts.dtsort_get_options(h)
         o.launch_mode = args.launch_mode
+        o.block_tiles = args.block_tiles
+        o.gamma_max = args.gamma_max
+        o.finisher_capacity = args.capacity
         o.bucketing = {"digit": dts.DTSORT_BUCKETING_DIGIT,
                        "learned": dts.DTSORT_BUCKETING_LEARNED,
                        "learned-always": dts.DTSORT_BUCKETING_LEARNED_ALWAYS}[args.bucketing]

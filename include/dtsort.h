@@ -121,7 +121,7 @@ typedef struct {
                                 2: the persistent launch alone. */
   int32_t block_tiles;       /* rows of the per-level count matrix cover
                                 block_tiles tiles of the scatter (8K 32-bit or
-                                4K 64-bit keys each); 1..8, default 4 */
+                                4K 64-bit keys each); 1..8, default 8 */
   int32_t reserved[4];
 } dtsort_options;
 

@@ -79,7 +79,9 @@ cudaError_t get_shape(dtsort_handle h, int op, KernelShape **out) {
   return cudaSuccess;
 }
 
-Opts effective(const dtsort_options &o, const KernelShape &ks) {
+// nsegs: arrays in the call (a batch of several gets 4-tile blocks by default:
+// its small arrays fill large blocks badly; a single array gets ks.blk).
+Opts effective(const dtsort_options &o, const KernelShape &ks, int64_t nsegs = 1) {
   Opts r;
   r.gamma_max = o.gamma_max > 0 ? o.gamma_max : dts::GAMMA_HW;
   r.cap = (o.finisher_capacity > 0 && o.finisher_capacity < ks.fin_cap) ? o.finisher_capacity
@@ -88,7 +90,8 @@ Opts effective(const dtsort_options &o, const KernelShape &ks) {
   r.sample_factor = o.sample_log_factor > 0 ? o.sample_log_factor : 1;
   r.seed = o.seed ? o.seed : 1;
   r.debug_fault = o.debug_fault;
-  r.blk_tiles = o.block_tiles > 0 ? o.block_tiles : ks.blk / ks.tile;
+  r.blk_tiles = o.block_tiles > 0 ? o.block_tiles
+                                   : (nsegs > 1 ? std::min(4, ks.blk / ks.tile) : ks.blk / ks.tile);
   r.wait_ns = (unsigned long long)(o.wait_limit_ms > 0 ? o.wait_limit_ms : 2000) * 1000000ull;
   return r;
 }
@@ -350,7 +353,7 @@ dtsort_status run_sort(dtsort_handle h, int op, void *keys, void *vals, const in
   cudaError_t e = get_shape(h, op, &ks);
   if (e != cudaSuccess) return DTSORT_ERR_CUDA;
   if (ks->blocks_per_sm < 1) return DTSORT_ERR_UNSUPPORTED;
-  const Opts o = effective(tuned_options(h, op, n, offsets ? nsegs : 1), *ks);
+  const Opts o = effective(tuned_options(h, op, n, offsets ? nsegs : 1), *ks, offsets ? nsegs : 1);
   Layout L = make_layout(kb, vb, n, offsets ? nsegs : 1, o, *ks);
   const bool learned = allow_learned &&
                        (h->opt.bucketing == DTSORT_BUCKETING_LEARNED ||
@@ -586,9 +589,17 @@ dtsort_status dtsort_workspace_bytes(dtsort_handle h, dtsort_op op, int64_t n,
   if (cur != h->device && cudaSetDevice(h->device) != cudaSuccess) return DTSORT_ERR_CUDA;
   KernelShape *ks = nullptr;
   if (get_shape(h, op, &ks) != cudaSuccess) return DTSORT_ERR_CUDA;
-  const Opts o = effective(tuned_options(h, op, n, num_segments > 0 ? num_segments : 1), *ks);
+  const int64_t ns = num_segments > 0 ? num_segments : 1;
   const int kb = key_bytes(op), vb = has_vals(op) ? kb : 0;
-  Layout L = make_layout(kb, vb, n, num_segments > 0 ? num_segments : 1, o, *ks);
+  // the larger of the single-array and the batch default block sizes, so that
+  // a call of either kind fits
+  const dtsort_options to = tuned_options(h, op, n, ns);
+  Layout L = make_layout(kb, vb, n, ns, effective(to, *ks, 1), *ks);
+  {
+    const Layout L2 = make_layout(kb, vb, n, ns, effective(to, *ks, 2), *ks);
+    if (L2.total > L.total) L = L2;
+  }
+  const Opts o = effective(to, *ks, ns);
   if ((h->opt.bucketing == DTSORT_BUCKETING_LEARNED ||
        h->opt.bucketing == DTSORT_BUCKETING_LEARNED_ALWAYS) &&
       n >= kLrnMinN) {
@@ -717,7 +728,7 @@ dtsort_status dtsort_get_stats(dtsort_handle h, dtsort_stats *out) {
 // Candidate settings tried by the autotuner.
 static const int kTuneGamma[] = {7, 8, 9};
 static const int kTuneCapDiv[] = {4, 3, 2};  // capacity = fin_cap * 2 / div
-static const int kTuneBlk[] = {2, 4};
+static const int kTuneBlk[] = {4, 8};
 
 dtsort_status dtsort_autotune_scratch_bytes(dtsort_handle h, dtsort_op op, int64_t n,
                                             int64_t num_segments, size_t *bytes) {

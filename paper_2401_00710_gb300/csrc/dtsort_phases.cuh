@@ -27,7 +27,7 @@ struct Shape {
   static constexpr int FIN_NBW = FIN_NBIN + NT;         // words of the padded bins
   static constexpr int FIN_CMAX = 16;                   // largest bin sorted in place
   static constexpr int STAGE = TILE * KB;               // scatter staging (keys or values)
-  static constexpr int BLK_TILES = 4;                   // tiles per count-matrix row
+  static constexpr int BLK_TILES = 8;                   // tiles per count-matrix row
   static constexpr int BLK = BLK_TILES * TILE;          // records per block
   static constexpr int CH = 32;                         // rows per look-back chunk
 };
@@ -1051,11 +1051,13 @@ __device__ void phase_finish(const Params &P, int level, unsigned char *smem) {
       __syncthreads();
       continue;
     }
-    // one counting pass on the top fb bits of key - kmin (2^fb bins, n to 2n
-    // of them): histogram, bin starts, placement in arbitrary order inside a
-    // bin; the write-out then ranks each record among its bin's records by
-    // (key, original index), which gives the stable order
-    const int fb = min(max(bitlen64((uint64_t)(n - 1)), 9), S::FIN_FB);
+    // one counting pass on the top fb bits of key - kmin (2^fb bins, 2n to
+    // 4n of them where shared memory allows: fewer records share a bin, so
+    // the in-bin ranking below rarely loops): histogram, bin starts,
+    // placement in arbitrary order inside a bin; the write-out then ranks
+    // each record among its bin's records by (key, original index), which
+    // gives the stable order
+    const int fb = min(max(bitlen64((uint64_t)(n - 1)) + 1, 9), S::FIN_FB);
     const int psh = fb - 9;                 // log2 bins per thread
     const int per = 1 << psh;
     const int bsh = bitlen64(span) > fb ? bitlen64(span) - fb : 0;

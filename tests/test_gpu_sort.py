@@ -339,8 +339,9 @@ def test_argument_checks(G):
 def test_bounded_wait_expires_without_hanging(G):
     # a look-back chunk that never publishes its status: the successors'
     # waits run out, the sort latches DEVICE_TIMEOUT and the context stays
-    # usable (3M records = several chunks of the level-0 count matrix)
-    n = 3_000_000
+    # usable (6M records = 3 chunks of 32 rows of 64K-record blocks in the
+    # level-0 count matrix: chunk 2 waits on the muted chunk 1)
+    n = 6_000_000
     keys = gen.family("uniform", n, np.uint32, seed=4)
     vals = gen.iota(n, np.uint32)
     G.set_options(debug_fault=1, wait_limit_ms=50)
