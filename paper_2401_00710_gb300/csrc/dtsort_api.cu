@@ -474,10 +474,10 @@ dtsort_status run_sort(dtsort_handle h, int op, void *keys, void *vals, const in
   const int head = (h->opt.launch_mode == 0 && !offsets)
                        ? predict_levels(n, 8 * kb, o, L.target) : 0;
   switch (op) {
-    case DTSORT_OP_U32: e = dts::launch_u32(P, grid, head, s); break;
-    case DTSORT_OP_U32_KV: e = dts::launch_u32kv(P, grid, head, s); break;
-    case DTSORT_OP_U64: e = dts::launch_u64(P, grid, head, s); break;
-    default: e = dts::launch_u64kv(P, grid, head, s); break;
+    case DTSORT_OP_U32: e = dts::launch_u32(P, grid, head, *ks, h->nsm, s); break;
+    case DTSORT_OP_U32_KV: e = dts::launch_u32kv(P, grid, head, *ks, h->nsm, s); break;
+    case DTSORT_OP_U64: e = dts::launch_u64(P, grid, head, *ks, h->nsm, s); break;
+    default: e = dts::launch_u64kv(P, grid, head, *ks, h->nsm, s); break;
   }
   h->launches += 1 + (head > 0 ? 1 + 7 * (int64_t)head : 0);
   return from_cuda(e);

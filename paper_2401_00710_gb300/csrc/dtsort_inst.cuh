@@ -16,9 +16,12 @@ cudaError_t DTS_CAT(shape_, DTS_NAME)(KernelShape *out) {
                                        (int)smem);
   if (e != cudaSuccess) return e;
   // the per-phase kernels too, here and not at launch (launches may be
-  // captured into a graph)
-  const void *pk[] = {
-      (const void *)dtsort_phase_kernel<DTS_K, DTS_HV>,
+  // captured into a graph): the combined one with the largest shared memory,
+  // each single-phase one with its own, and how many CTAs of it an SM holds
+  e = cudaFuncSetAttribute(dtsort_phase_kernel<DTS_K, DTS_HV>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const void *pk[8] = {
       (const void *)dtsort_phase_one<DTS_K, DTS_HV, KP_SEED>,
       (const void *)dtsort_phase_one<DTS_K, DTS_HV, KP_SETUP>,
       (const void *)dtsort_phase_one<DTS_K, DTS_HV, KP_SAMPLE>,
@@ -27,9 +30,14 @@ cudaError_t DTS_CAT(shape_, DTS_NAME)(KernelShape *out) {
       (const void *)dtsort_phase_one<DTS_K, DTS_HV, KP_SCAN>,
       (const void *)dtsort_phase_one<DTS_K, DTS_HV, KP_SCATTER>,
       (const void *)dtsort_phase_one<DTS_K, DTS_HV, KP_FINISH>};
-  for (const void *f : pk) {
-    e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  for (int ph = 0; ph < 8; ++ph) {
+    const size_t sm = phase_smem_bytes<DTS_K, DTS_HV>(ph);
+    e = cudaFuncSetAttribute(pk[ph], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
+    int b = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, pk[ph], NT, sm);
+    if (e != cudaSuccess) return e;
+    out->phase_blocks[ph] = b < phase_min_blocks(ph) ? b : phase_min_blocks(ph);
   }
   int nb = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, NT, smem);
@@ -47,12 +55,16 @@ cudaError_t DTS_CAT(shape_, DTS_NAME)(KernelShape *out) {
 // synchronisation; each phase checks on the device whether it has work), then
 // the persistent kernel for the remaining levels and the merges.  head = 0:
 // the persistent kernel alone.
-cudaError_t DTS_CAT(launch_, DTS_NAME)(const Params &P, int grid, int head, cudaStream_t s) {
+cudaError_t DTS_CAT(launch_, DTS_NAME)(const Params &P, int grid, int head, const KernelShape &ks,
+                                       int nsm, cudaStream_t s) {
   const size_t smem = smem_bytes<DTS_K, DTS_HV>();
   cudaError_t e;
   if (head > 0) {
-    // one kernel per phase (attributes set by shape_)
-    auto run = [&](int phase, int level, int g, int prev) {
+    // one kernel per phase (attributes set by shape_), each with its own
+    // shared memory and as many CTAs as an SM holds of it
+    auto run = [&](int phase, int level, int g0, int prev) {
+      const int g = g0 == 1 ? 1 : nsm * (ks.phase_blocks[phase] > 0 ? ks.phase_blocks[phase] : 1);
+      const size_t smem = phase_smem_bytes<DTS_K, DTS_HV>(phase);
       switch (phase) {
         case KP_SEED: dtsort_phase_one<DTS_K, DTS_HV, KP_SEED><<<g, NT, smem, s>>>(P, level, prev); break;
         case KP_SETUP: dtsort_phase_one<DTS_K, DTS_HV, KP_SETUP><<<g, NT, smem, s>>>(P, level, prev); break;

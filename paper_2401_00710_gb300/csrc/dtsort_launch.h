@@ -17,10 +17,12 @@ struct KernelShape {
   int ch;    // rows per look-back chunk
   size_t smem;
   int blocks_per_sm;
+  int phase_blocks[8];  // CTAs per SM of each single-phase kernel (queued levels)
 };
 
 #define DTS_DECLARE(NAME)                                                      \
-  cudaError_t launch_##NAME(const Params &P, int grid, int head, cudaStream_t s); \
+  cudaError_t launch_##NAME(const Params &P, int grid, int head, const KernelShape &ks, \
+                            int nsm, cudaStream_t s);                          \
   cudaError_t launch_split_##NAME(const Params &P, int grid, cudaStream_t s,   \
                                   void *ctl_host, int *launches);              \
   cudaError_t shape_##NAME(KernelShape *out);

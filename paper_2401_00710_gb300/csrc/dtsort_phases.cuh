@@ -99,6 +99,37 @@ constexpr size_t smem_bytes() {
   return m > smp ? m : smp;
 }
 
+// Dynamic shared memory of one phase's own kernel (the queued levels launch
+// each phase as its own kernel; the light phases then fit more CTAs per SM).
+template <typename K, bool HV>
+constexpr size_t phase_smem_bytes(int ph) {
+  // histogram: tables + one count row
+  const size_t hist = 64 + sizeof(SegTables<K>) + 16 + 4 * ((1 << GAMMA_HW) + 1) + 16 +
+                      sizeof(K) * HASH_HW + 16 + 2 * HASH_HW + 16 + 4 * NB_PAD + 16 +
+                      sizeof(K) * (1 << GAMMA_HW) + 16 + 4 * (LRN_TAB_N + 1) + 256;
+  // sample: the on-chip sample and its tables
+  const size_t smp = 16 + sizeof(K) * SMAX + 16 + sizeof(K) * (SMAX / 2 + 8) + 16 + 4 * 1024 +
+                     16 + sizeof(K) * HASH_HW + 16 + 2 * HASH_HW + 512;
+  // bucket scan: counts, offsets, light table
+  const size_t scan = 16 + 8 * NB_PAD + 16 + 8 * (NB_PAD + 1) + 16 + 4 * ((1 << GAMMA_HW) + 1) +
+                      16 + 8 * (NWARP + 1) + 256;
+  switch (ph) {
+    case 2: return smp;                        // KP_SAMPLE
+    case 3: return hist;                       // KP_HIST
+    case 4: return 64 + sizeof(SegInfo) + 256;  // KP_MSCAN
+    case 5: return scan;                       // KP_SCAN
+    case 0:                                    // KP_SEED
+    case 1: return 8 * (NWARP + 1) + 256;      // KP_SETUP
+    default: return smem_bytes<K, HV>();       // scatter, base case
+  }
+}
+
+// CTAs per SM the per-phase kernels are built for: the light phases 3, the
+// scatter and the base case 2 (their shared memory allows no more).
+__host__ __device__ constexpr int phase_min_blocks(int ph) {
+  return (ph >= 2 && ph <= 5) ? 3 : 2;
+}
+
 // ----------------------------------------------------------------- queues
 __device__ __forceinline__ void push_task(const Params &P, const Task &t) {
   long long i = atomic_add_ll(&P.ctl->ntasks, 1ll);
@@ -1604,8 +1635,8 @@ __global__ void __launch_bounds__(NT, 2) dtsort_phase_kernel(const __grid_consta
 // records that the level is done.  prev_kind >= 0: the phase-time bucket the
 // time since the previous launch's start goes to.
 template <typename K, bool HV, int PH>
-__global__ void __launch_bounds__(NT, 2) dtsort_phase_one(const __grid_constant__ Params P,
-                                                          int level, int prev_kind) {
+__global__ void __launch_bounds__(NT, phase_min_blocks(PH))
+    dtsort_phase_one(const __grid_constant__ Params P, int level, int prev_kind) {
   Ctl *c = P.ctl;
   if (*(volatile int *)&c->error) return;
   if (PH >= KP_SETUP && PH <= KP_FINISH && level > 0 && ld_cg64(&c->nseg[level & 1]) == 0)
