@@ -90,6 +90,8 @@ def _declare(L):
         f.restype = _INT
     L.oracle_stable_positions.argtypes = [_P, _INT, _I64, _P, _I64, _P, _INT]
     L.oracle_stable_positions.restype = _INT
+    L.oracle_check_stable.argtypes = [_P, _P, _P, _INT, _INT, _I64, _INT]
+    L.oracle_check_stable.restype = _I64
     L.oracle_splitmix64_next.argtypes = [ctypes.POINTER(_U64)]
     L.oracle_splitmix64_next.restype = _U64
     L.oracle_splitmix64_at.argtypes = [_U64, _U64]
@@ -159,6 +161,20 @@ def stable_sort_segmented(keys, vals, offsets, nthreads=0):
          _ptr(ov), nthreads):
         raise ValueError("oracle segmented sort failed")
     return ok, ov
+
+
+def check_stable(keys_in, keys_out, idx_out, nthreads=0):
+    """-1 if (keys_out, idx_out) is the stable sort of keys_in (idx_out[i] =
+    original index of output record i), else the first failing output slot
+    (len(keys_in) if some index is missing)."""
+    keys_in = np.ascontiguousarray(keys_in)
+    keys_out = np.ascontiguousarray(keys_out)
+    idx_out = np.ascontiguousarray(idx_out)
+    assert keys_in.dtype == keys_out.dtype and len(keys_in) == len(keys_out) == len(idx_out)
+    assert idx_out.dtype.itemsize in (4, 8)
+    return int(lib().oracle_check_stable(_ptr(keys_in), _ptr(keys_out), _ptr(idx_out),
+                                         _kbytes(keys_in), idx_out.dtype.itemsize,
+                                         len(keys_in), nthreads))
 
 
 def stable_positions(keys, js, nthreads=0):

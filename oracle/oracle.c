@@ -14,6 +14,12 @@
  *                            textbook merge sort on those pairs computes.
  *   oracle_stable_positions  The same definition for one record j:
  *                            pos(j) = #{i : k_i < k_j} + #{i < j : k_i == k_j}.
+ *   oracle_check_stable      The same definition read as a test of a claimed
+ *                            output (keys, and for each output slot the
+ *                            original index of its record): the pairs (key,
+ *                            index) must be strictly increasing, the indices a
+ *                            permutation of 0..n-1, and each key the input key
+ *                            at its index; exactly one output passes.
  *   oracle_splitmix64_*      The SplitMix64 generator (Steele, Lea, Flood,
  *                            OOPSLA 2014), used for the sampler's random draws.
  *   oracle_sample_*          Alg. 2 step 1 (Sec. 3.1): draw the sample S, sort
@@ -280,6 +286,67 @@ int oracle_stable_positions(const void *keys, int kbytes, int64_t n,
   }
   free(jobs); free(th); free(part);
   return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Check of a claimed stable-sorted output (Sec. 2.3 definition).            */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+  const void *kin, *kout;
+  const void *idx;     /* original index of each output record */
+  int kbytes, ibytes;
+  int64_t n, lo, hi;
+  unsigned char *seen; /* one byte per original index */
+  int64_t bad;         /* first failing output slot + 1, or 0 */
+} chk_job_t;
+
+static void *chk_main(void *arg) {
+  chk_job_t *j = (chk_job_t *)arg;
+  for (int64_t i = j->lo; i < j->hi && !j->bad; ++i) {
+    const uint64_t ix = key_at(j->idx, j->ibytes, i);
+    const uint64_t k = key_at(j->kout, j->kbytes, i);
+    int ok = ix < (uint64_t)j->n && key_at(j->kin, j->kbytes, (int64_t)ix) == k;
+    if (ok && i + 1 < j->n) {  /* (key, index) strictly increasing */
+      const uint64_t k2 = key_at(j->kout, j->kbytes, i + 1);
+      ok = k < k2 || (k == k2 && ix < key_at(j->idx, j->ibytes, i + 1));
+    }
+    /* strictly increasing pairs cannot repeat an index (an index fixes its
+       key), so the indices are distinct; `seen` confirms they cover 0..n-1 */
+    if (ok) j->seen[ix] = 1;
+    else j->bad = i + 1;
+  }
+  return NULL;
+}
+
+/* Returns -1 if the output is the stable sort of kin, else the first failing
+ * output slot (or n if some index never appears).  idx: indices of ibytes
+ * (4 or 8) bytes. */
+int64_t oracle_check_stable(const void *kin, const void *kout, const void *idx, int kbytes,
+                            int ibytes, int64_t n, int nthreads) {
+  if (n <= 0) return -1;
+  if (nthreads <= 0) nthreads = oracle_default_threads();
+  unsigned char *seen = (unsigned char *)calloc((size_t)n, 1);
+  chk_job_t *jobs = (chk_job_t *)calloc((size_t)nthreads, sizeof(chk_job_t));
+  pthread_t *th = (pthread_t *)calloc((size_t)nthreads, sizeof(pthread_t));
+  if (!seen || !jobs || !th) { free(seen); free(jobs); free(th); return -2; }
+  for (int t = 0; t < nthreads; ++t) {
+    jobs[t].kin = kin; jobs[t].kout = kout; jobs[t].idx = idx; jobs[t].kbytes = kbytes;
+    jobs[t].ibytes = ibytes;
+    jobs[t].n = n; jobs[t].lo = n * t / nthreads; jobs[t].hi = n * (t + 1) / nthreads;
+    jobs[t].seen = seen;
+    pthread_create(&th[t], NULL, chk_main, &jobs[t]);
+  }
+  int64_t first = -1;
+  for (int t = 0; t < nthreads; ++t) {
+    pthread_join(th[t], NULL);
+    if (jobs[t].bad && first < 0) first = jobs[t].bad - 1;
+  }
+  if (first < 0)
+    for (int64_t i = 0; i < n; ++i)
+      if (!seen[i]) { first = n; break; }
+  free(seen); free(jobs); free(th);
+  return first;
 }
 
 /* ------------------------------------------------------------------------ */

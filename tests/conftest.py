@@ -12,7 +12,7 @@ def pytest_configure(config):
     config.addinivalue_line(
         "markers", "gpu: needs a CUDA GPU (sm_103a); parity tests through the C-ABI")
     config.addinivalue_line(
-        "markers", "slow: long-running CPU test")
+        "markers", "slow: long-running test (full-size inputs)")
 
 
 def pytest_collection_modifyitems(config, items):

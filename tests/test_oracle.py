@@ -470,3 +470,37 @@ def test_planted_mistakes_are_caught(mutant, tmp_path):
     with oracle.using_library(str(so)):
         with pytest.raises(AssertionError):
             _run_pins()
+
+
+# ------------------------------------------------ check of a claimed output
+@pytest.mark.parametrize("dtype", [np.uint32, np.uint64])
+def test_check_stable_accepts_exactly_the_stable_sort(dtype):
+    # the checker (the definition read as a test) against numpy's stable
+    # argsort, and against plausible wrong outputs, each caught
+    n = 200_003
+    keys = gen.family("zipf1.2hash" if dtype == np.uint64 else "zipf1.0", n, dtype, seed=17)
+    order = np.argsort(keys, kind="stable")
+    ko, io = keys[order], order.astype(np.uint64 if dtype == np.uint64 else np.uint32)
+    assert oracle.check_stable(keys, ko, io) == -1
+    # two records of equal key in the wrong order
+    i = int(np.where(ko[1:] == ko[:-1])[0][0])
+    bad = io.copy()
+    bad[i], bad[i + 1] = bad[i + 1], bad[i]
+    assert oracle.check_stable(keys, ko, bad) == i
+    # two records of different keys swapped (keys and indices together)
+    j = int(np.where(ko[1:] != ko[:-1])[0][0])
+    kb, ib = ko.copy(), io.copy()
+    kb[j], kb[j + 1] = kb[j + 1], kb[j]
+    ib[j], ib[j + 1] = ib[j + 1], ib[j]
+    assert oracle.check_stable(keys, kb, ib) == j
+    # one record duplicated over its neighbour
+    dup = io.copy()
+    dup[j + 1] = dup[j]
+    assert oracle.check_stable(keys, ko, dup) >= 0
+    # a key changed, or an index out of range
+    kx = ko.copy()
+    kx[n // 2] ^= dtype(1)
+    assert oracle.check_stable(keys, kx, io) >= 0
+    ix = io.copy()
+    ix[-1] = n
+    assert oracle.check_stable(keys, ko, ix) == n - 1
