@@ -28,6 +28,7 @@ constexpr int GAMMA_HW = 9;                   // widest digit of one level
 constexpr int HEAVY_HW = 128;                 // heavy keys kept per subproblem
 constexpr int NB_HW = (1 << GAMMA_HW) + HEAVY_HW + 1;  // 641
 constexpr int NB_PAD = 648;                   // NB_HW + dummy bucket, padded
+constexpr int NB_PAIR = NB_PAD / 2;           // 16-bit warp counters, two per word
 constexpr int LRN_TAB_N = 512;                // learned prediction table cells
 constexpr int SMAX = 8192;                    // largest on-chip sample
 constexpr int HASH_HW = 1 << GAMMA_HW;        // hash slots for <= 256 heavy keys
@@ -36,6 +37,7 @@ constexpr int64_t COPY_CHUNK = 1 << 16;       // records per plain-copy task
 constexpr int MERGE_CHUNK = 8192;             // output records per merge item
 constexpr int FIN_DIG = 8;                    // base-case digit bits
 constexpr int FIN_NB = (1 << FIN_DIG) + 8;    // 256 digits + dummy, padded
+constexpr int FIN_IB = 13;                    // index bits of a base-case composite
 constexpr uint16_t HEMPTY = 0xFFFF;
 
 enum { ERR_INVALID = 1, ERR_TIMEOUT = 4, ERR_INTERNAL = 6 };
@@ -395,6 +397,62 @@ __device__ __forceinline__ unsigned warp_rank_slots(unsigned b, unsigned *slot, 
   __syncwarp();
   old = __shfl_sync(0xffffffffu, old, leader);
   return old + __popc(peers & lanemask_lt());
+}
+
+// Half b & 1 of a word holding two 16-bit counts (bucket b's count).
+__device__ __forceinline__ unsigned half16(unsigned word, unsigned b) {
+  return (word >> ((b & 1u) << 4)) & 0xFFFFu;
+}
+
+// Stable rank among this warp's earlier items (in (round, lane) order) with
+// the same bucket b.  Every lane ORs its bit into its bucket's slot and reads
+// back the set of peers; the lowest peer advances the bucket's running count
+// with one shared atomic (the count before this round is shuffled to the
+// peers) and clears the slot.  The next round's atomic is issued after this
+// one has returned, so the counts of one bucket advance in round order.  A
+// round whose lanes all share one bucket skips the slot.  slot: this warp's
+// slots (zero on entry, zero again on return); wc2: this warp's running
+// counts, 16 bits each, two per word (bucket b in half b & 1 of word b >> 1).
+__device__ __forceinline__ unsigned warp_rank(unsigned b, unsigned *slot, unsigned *wc2) {
+  const unsigned lane = threadIdx.x & 31;
+  const unsigned b0 = __shfl_sync(0xffffffffu, b, 0);
+  unsigned peers;
+  const bool one = __all_sync(0xffffffffu, b == b0);
+  if (one) {
+    peers = 0xffffffffu;
+  } else {
+    atomicOr(&slot[b], 1u << lane);
+    __syncwarp();
+    peers = slot[b];
+  }
+  const unsigned leader = __ffs(peers) - 1;
+  unsigned old = 0;
+  if (lane == leader) {
+    const unsigned sh = (b & 1u) << 4;
+    old = atomicAdd(&wc2[b >> 1], (unsigned)__popc(peers) << sh) >> sh;
+  }
+  old = __shfl_sync(0xffffffffu, old, leader) & 0xFFFFu;
+  if (!one) {
+    if (lane == leader) slot[b] = 0u;
+    __syncwarp();
+  }
+  return old + __popc(peers & lanemask_lt());
+}
+
+// Asks L2 to fetch elements [first, first + count) of array a (clipped to
+// [0, n)): one bulk prefetch of the 16-byte aligned part of the range.  A
+// hint only: nothing waits for it, and it touches no address outside a.
+template <typename K>
+__device__ __forceinline__ void prefetch_l2(const K *a, int64_t first, int64_t count, int64_t n) {
+  int64_t e = first + count;
+  if (first < 0) first = 0;
+  if (e > n) e = n;
+  if (e <= first) return;
+  const uintptr_t lo = ((uintptr_t)(a + first) + 15) & ~(uintptr_t)15;
+  const uintptr_t hi = (uintptr_t)(a + e) & ~(uintptr_t)15;
+  if (hi <= lo) return;
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(lo), "r"((unsigned)(hi - lo))
+               : "memory");
 }
 
 // Digit width for a subproblem of size s whose keys have hi unsorted bits:

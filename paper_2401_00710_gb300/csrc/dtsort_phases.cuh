@@ -14,17 +14,10 @@ struct Shape {
   static constexpr int TILE = NT * ITEMS;
   static constexpr int FIN_CAP = (96 * 1024) / (2 * (KB + VB)) < 6144
                                       ? (96 * 1024) / (2 * (KB + VB)) : 6144;
-  static constexpr int FIN_BYTES = 2 * FIN_CAP * (KB + VB);  // base-case buffers
+  // base-case area: the two record buffers of the LSD passes, or the one-pass
+  // bins, placed composites and values (see fin_onepass)
+  static constexpr int FIN_BYTES = 96 * 1024;
   static constexpr int FIN_IT = FIN_CAP / NT;           // base-case items / thread
-  // one-pass base case: up to 2^FIN_FB bins over the task's key range, plus
-  // (with values) the records' original indices, in the first record buffer
-  // (each thread's run of bins is followed by one pad word, so that the
-  // lanes of a warp walking their runs hit distinct banks)
-  static constexpr int FIN_FB =
-      4 * (8192 + NT) + (HV ? 2 * FIN_CAP : 0) <= FIN_CAP * (KB + VB) ? 13 : 12;
-  static constexpr int FIN_NBIN = 1 << FIN_FB;
-  static constexpr int FIN_PER = FIN_NBIN / NT;         // most bins per thread
-  static constexpr int FIN_NBW = FIN_NBIN + NT;         // words of the padded bins
   static constexpr int FIN_CMAX = 16;                   // largest bin sorted in place
   static constexpr int STAGE = TILE * KB;               // scatter staging (keys or values)
   static constexpr int BLK_TILES = 8;                   // tiles per count-matrix row
@@ -61,16 +54,14 @@ struct Carve {
   }
 };
 
-// Bytes of the scatter's shared area: ranking slots, or a staged tile (keys
-// with their destinations, or keys with their values).
+// Bytes of the scatter's staged tile (keys with their destinations, or keys
+// with their values).
 template <typename K, bool HV>
 __host__ __device__ constexpr int scatter_area() {
   using S = Shape<K, HV>;
-  constexpr int slots = 4 * NWARP * NB_PAD;
   constexpr int kd = S::TILE * (int)sizeof(K) + 4 * S::TILE;
   constexpr int kv = HV ? 2 * S::TILE * (int)sizeof(K) : 0;
-  constexpr int m = slots > kd ? slots : kd;
-  return m > kv ? m : kv;
+  return kd > kv ? kd : kv;
 }
 
 template <typename K, bool HV>
@@ -81,9 +72,9 @@ constexpr size_t smem_bytes() {
   sc += 64 + sizeof(SegTables<K>);
   sc += 16 + 4 * ((1 << GAMMA_HW) + 1);            // lid
   sc += 16 + sizeof(K) * HASH_HW + 16 + 2 * HASH_HW;  // hash
-  sc += 16 + 2 * (size_t)NWARP * NB_PAD;           // warp counters
-  sc += 4 * (16 + 4 * NB_PAD);                     // tile counts/offsets, bases
-  sc += 16 + (size_t)scatter_area<K, HV>();  // rank slots / staged tile
+  sc += 16 + 4 * (size_t)NWARP * NB_PAIR;          // warp counters
+  sc += 3 * (16 + 4 * NB_PAD);                     // tile offsets, bases
+  sc += 16 + (size_t)scatter_area<K, HV>();        // staged tile
   sc += 16 + 8 * (NWARP + 1) + 256;
   sc += 16 + sizeof(K) * (1 << GAMMA_HW) + 16 + 4 * (LRN_TAB_N + 1);  // learned tables
   // base case
@@ -91,7 +82,7 @@ constexpr size_t smem_bytes() {
   fin += 16 + (size_t)S::FIN_BYTES;
   fin += 16 + 2 * (size_t)NWARP * FIN_NB;
   fin += 16 + 4 * FIN_NB * 2;
-  fin += 16 + 8 * (NWARP + 1) + 256;
+  fin += 16 + 4 * (NWARP + 1) + 16 + 4 * NWARP + 4 * 16 + 256;
   // sampler
   size_t smp = 16 + sizeof(K) * SMAX + 16 + sizeof(K) * (SMAX / 2 + 8) + 16 + 4 * 1024 +
                16 + sizeof(K) * HASH_HW + 16 + 2 * HASH_HW + 512;
@@ -519,6 +510,7 @@ __device__ void phase_hist(const Params &P, int level, unsigned char *smem) {
       if (tb >= brem) break;
       const int tn = brem - tb < S::TILE ? (int)(brem - tb) : S::TILE;
       const K *ts = src + b0 + tb;
+      if (threadIdx.x == 0) prefetch_l2<K>(src, b0 + tb + S::TILE, S::TILE, P.n);
       K key[S::ITEMS];
 #pragma unroll
       for (int j = 0; j < S::ITEMS; ++j) {
@@ -752,6 +744,9 @@ __device__ void phase_scan(const Params &P, int level, unsigned char *smem) {
 // warp in input order and staged in shared memory in bucket order so that
 // each bucket's run is written contiguously.  A subproblem without heavy keys
 // whose digit reaches its top unsorted bit needs no table: bucket = digit.
+// Per tile: clear the peer slots | barrier | rank (warp counters) | barrier |
+// prefix over warps + tile scan (one barrier inside) | barrier | stage |
+// barrier | write-out (the warp counters are cleared meanwhile) | barrier.
 template <typename K, bool HV>
 __device__ void phase_scatter(const Params &P, int level, unsigned char *smem) {
   using S = Shape<K, HV>;
@@ -768,25 +763,28 @@ __device__ void phase_scatter(const Params &P, int level, unsigned char *smem) {
   int32_t *lid_s = cv.take<int32_t>((1 << GAMMA_HW) + 1);
   K *hk_s = cv.take<K>(HASH_HW);
   uint16_t *hid_s = cv.take<uint16_t>(HASH_HW);
-  uint16_t *wcnt = cv.take<uint16_t>(NWARP * NB_PAD);
-  unsigned *tcnt = cv.take<unsigned>(NB_PAD);
+  unsigned *wc2 = cv.take<unsigned>(NWARP * NB_PAIR);  // warp counters, 16-bit pairs
   unsigned *toff = cv.take<unsigned>(NB_PAD);
   unsigned *gbase = cv.take<unsigned>(NB_PAD);
   unsigned *base = cv.take<unsigned>(NB_PAD);
   unsigned *sh = cv.take<unsigned>(NWARP + 1);
   K *spl_s = cv.take<K>(1 << GAMMA_HW);
   float *tab_s = cv.take<float>(LRN_TAB_N + 1);
-  // ranking slots and the staged tile share one area (never live together);
-  // the staged tile is keys + destinations, or keys + values on the fast path
+  // the staged tile: keys + destinations, or keys + values on the fast path
   constexpr int AREA = scatter_area<K, HV>();
   unsigned char *area = cv.take<unsigned char>(AREA);
-  unsigned *slots = (unsigned *)area;
   K *stage = (K *)area;
   unsigned *dest = (unsigned *)(area + S::TILE * sizeof(K));  // offset in the subproblem
+  // the ranking's peer slots use the staging area too (cleared before each
+  // tile is ranked, after the previous tile's write-out has finished)
+  static_assert(AREA >= 4 * NWARP * NB_PAD, "slots fit in the staging area");
+  unsigned *slots = (unsigned *)area;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   unsigned bad = 0;  // self-check: a slot or destination out of range, reported once
-  uint16_t *mywc = wcnt + w * NB_PAD;
+  unsigned *mywc = wc2 + w * NB_PAIR;
   unsigned *myslot = slots + w * NB_PAD;
+  for (int i = threadIdx.x; i < NWARP * NB_PAIR; i += NT) wc2[i] = 0u;
+  __syncthreads();
   const int64_t r0 = nblocks * blockIdx.x / gridDim.x;
   const int64_t r1 = nblocks * (blockIdx.x + 1) / gridDim.x;
   // the current subproblem and the end of its blocks, in registers: T is
@@ -803,6 +801,7 @@ __device__ void phase_scatter(const Params &P, int level, unsigned char *smem) {
       cur_end = T.info.blk0 + T.info.nblk;
     }
     const int nb = T.info.nb;
+    const int npair = (nb + 2) / 2;  // pairs covering buckets 0..nb (nb: the dummy)
     const int lo = T.info.lo;
     const unsigned gmask = (1u << (T.info.t - T.info.lo)) - 1u;
     const bool fast = T.info.hbits == 0 && T.info.t >= T.hi && !T.info.learned;
@@ -823,12 +822,6 @@ __device__ void phase_scatter(const Params &P, int level, unsigned char *smem) {
       if (tb >= brem) break;
       const int tn = brem - tb < S::TILE ? (int)(brem - tb) : S::TILE;
       const int64_t tbase = b0 + tb;
-      {
-        uint4 *z = (uint4 *)wcnt;
-        for (int i = threadIdx.x; i < NWARP * NB_PAD * 2 / 16; i += NT) z[i] = make_uint4(0, 0, 0, 0);
-        uint4 *z2 = (uint4 *)slots;
-        for (int i = threadIdx.x; i < NWARP * NB_PAD * 4 / 16; i += NT) z2[i] = make_uint4(0, 0, 0, 0);
-      }
       K key[S::ITEMS];
       unsigned br[S::ITEMS];  // bucket << 16 | rank within warp, later the slot
 #pragma unroll
@@ -836,13 +829,24 @@ __device__ void phase_scatter(const Params &P, int level, unsigned char *smem) {
         const int i = w * 32 * S::ITEMS + j * 32 + lane;
         key[j] = i < tn ? ld_key<K>(src + tbase + i) : (K)0;
       }
+      // 64-bit keys: the next tile into L2 while this one is ranked (with
+      // 32-bit keys this measured slower: 16.3 -> 16.8 ms for the two
+      // scatters of 10^9 key/value pairs, against 26.0 -> 24.0 ms for 64-bit)
+      if (sizeof(K) == 8 && threadIdx.x == 0) {
+        prefetch_l2<K>(src, tbase + S::TILE, S::TILE, P.n);
+        if constexpr (HV) prefetch_l2<K>(vsrc, tbase, 2 * S::TILE, P.n);  // this and the next
+      }
+      {
+        uint4 *z = (uint4 *)slots;
+        for (int i = threadIdx.x; i < NWARP * NB_PAD / 4; i += NT) z[i] = make_uint4(0, 0, 0, 0);
+      }
       __syncthreads();
       if (fast) {
 #pragma unroll
         for (int j = 0; j < S::ITEMS; ++j) {
           const int i = w * 32 * S::ITEMS + j * 32 + lane;
           const unsigned b = i < tn ? fast_digit<K>(key[j], kbase, lo, gmask) : (unsigned)nb;
-          br[j] = (b << 16) | warp_rank_slots(b, myslot, mywc);
+          br[j] = (b << 16) | warp_rank(b, myslot, mywc);
         }
       } else {
 #pragma unroll
@@ -850,34 +854,44 @@ __device__ void phase_scatter(const Params &P, int level, unsigned char *smem) {
           const int i = w * 32 * S::ITEMS + j * 32 + lane;
           const unsigned b =
               i < tn ? bucket_of<K>(X, lid_s, hk_s, hid_s, key[j], spl_s, tab_s) : (unsigned)nb;
-          br[j] = (b << 16) | warp_rank_slots(b, myslot, mywc);
+          br[j] = (b << 16) | warp_rank(b, myslot, mywc);
         }
       }
       __syncthreads();
-      // per bucket: exclusive prefix over warps, tile total
-      for (int b = threadIdx.x; b < nb; b += NT) {
-        unsigned run = 0;
-#pragma unroll
-        for (int q = 0; q < NWARP; ++q) {
-          const unsigned x = wcnt[q * NB_PAD + b];
-          wcnt[q * NB_PAD + b] = (uint16_t)run;
-          run += x;
-        }
-        tcnt[b] = run;
-      }
-      __syncthreads();
+      // per bucket pair (2p, 2p+1): exclusive prefix over warps, tile counts,
+      // then the tile offsets (exclusive scan over buckets) and bases
       {
-        const int i0 = 2 * threadIdx.x, i1 = i0 + 1;
-        const unsigned v0 = i0 < nb ? tcnt[i0] : 0u, v1 = i1 < nb ? tcnt[i1] : 0u;
-        unsigned tot;
-        const unsigned o = block_excl_scan<unsigned>(v0 + v1, sh, tot);
-        if (i0 < NB_PAD) toff[i0] = o;
-        if (i1 < NB_PAD) toff[i1] = o + v0;
-      }
-      __syncthreads();
-      for (int b = threadIdx.x; b < nb; b += NT) {
-        gbase[b] = base[b] - toff[b];
-        base[b] += tcnt[b];
+        const int p = threadIdx.x;
+        unsigned run = 0;
+        if (p < npair) {
+#pragma unroll
+          for (int q = 0; q < NWARP; ++q) {
+            const unsigned x = wc2[q * NB_PAIR + p];
+            wc2[q * NB_PAIR + p] = run;
+            run += x;
+          }
+        }
+        const unsigned c0 = run & 0xFFFFu, c1 = run >> 16;
+        const unsigned v = c0 + c1;
+        unsigned x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+          if (lane >= o) x += y;
+        }
+        if (lane == 31) sh[w] = x;
+        __syncthreads();
+        if (p < npair) {
+          unsigned off = x - v;
+          for (int q = 0; q < w; ++q) off += sh[q];
+          const int b = 2 * p;
+          toff[b] = off;
+          toff[b + 1] = off + c0;
+          gbase[b] = base[b] - off;
+          gbase[b + 1] = base[b + 1] - off - c0;
+          base[b] += c0;
+          base[b + 1] += c1;
+        }
       }
       __syncthreads();
       if (fast) {
@@ -890,7 +904,7 @@ __device__ void phase_scatter(const Params &P, int level, unsigned char *smem) {
           const int i = w * 32 * S::ITEMS + j * 32 + lane;
           if (i < tn) {
             const unsigned b = br[j] >> 16;
-            const unsigned pj = toff[b] + wcnt[w * NB_PAD + b] + (br[j] & 0xFFFFu);
+            const unsigned pj = toff[b] + half16(mywc[b >> 1], b) + (br[j] & 0xFFFFu);
             if (b >= (unsigned)nb || pj >= (unsigned)tn) {
               bad = 1u + pj;
               br[j] = 0xFFFFFFFFu;
@@ -908,6 +922,7 @@ __device__ void phase_scatter(const Params &P, int level, unsigned char *smem) {
           }
         }
         __syncthreads();
+        for (int i = threadIdx.x; i < NWARP * NB_PAIR; i += NT) wc2[i] = 0u;
         for (int q = threadIdx.x; q < tn; q += NT) {
           const K k = stage[q];
           const unsigned d = gbase[fast_digit<K>(k, kbase, lo, gmask)] + (unsigned)q;
@@ -928,7 +943,7 @@ __device__ void phase_scatter(const Params &P, int level, unsigned char *smem) {
         const int i = w * 32 * S::ITEMS + j * 32 + lane;
         if (i < tn) {
           const unsigned b = br[j] >> 16;
-          const unsigned pj = toff[b] + wcnt[w * NB_PAD + b] + (br[j] & 0xFFFFu);
+          const unsigned pj = toff[b] + half16(mywc[b >> 1], b) + (br[j] & 0xFFFFu);
           if (b >= (unsigned)nb || pj >= (unsigned)tn) {
             bad = 1u + pj;
             br[j] = 0;
@@ -949,6 +964,7 @@ __device__ void phase_scatter(const Params &P, int level, unsigned char *smem) {
         }
       }
       __syncthreads();
+      for (int i = threadIdx.x; i < NWARP * NB_PAIR; i += NT) wc2[i] = 0u;
       for (int q = threadIdx.x; q < tn; q += NT) {
         const unsigned d = dest[q];
         if (d < seg_size) dseg[d] = stage[q];
@@ -974,6 +990,140 @@ __device__ void phase_scatter(const Params &P, int level, unsigned char *smem) {
 }
 
 // ------------------------------------------------------- base case + copy
+// Bins of the one-pass base case for composites of type CT: the most
+// (2^9..2^13) whose padded counters fit in the base-case area beside the
+// placed composites and, with values, the values in input order.
+template <typename K, bool HV, typename CT>
+__host__ __device__ constexpr int fin_fb() {
+  using S = Shape<K, HV>;
+  int fb = 13;
+  while (fb > 9 && 4 * ((1 << fb) + NT) + 32 + S::FIN_CAP * ((int)sizeof(CT) + S::VB) >
+                       S::FIN_BYTES)
+    --fb;
+  return fb;
+}
+
+// One-pass base case of a task of n <= FIN_CAP records held in registers
+// (item j of thread t is record i = j NT + t), keys in [kmin, kmin + 2^bl).
+// Each record becomes the composite c = (key - kmin) << FIN_IB | i (without
+// values c = key - kmin).  With values the composites are distinct and their
+// order is the order of (key, original index), i.e. the stable order.  A
+// counting pass on the top fb bits of key - kmin places the composites by bin
+// (in arbitrary order inside a bin); the thread that owns a run of bins then
+// sorts each of its bins that holds more than one record (insertion sort:
+// bins hold about half a record on average), and the write-out is a plain
+// coalesced copy of the placed order, the value taken from the input-order
+// copy by the composite's index.  The caller has zeroed the bins and holds
+// barrier-separated parity copies of the shared scalars.  Returns false,
+// having written nothing to global memory, when a bin holds more than
+// FIN_CMAX records.
+template <typename K, bool HV, typename CT>
+__device__ __forceinline__ bool fin_onepass(const Rec<K, HV> (&rr)[Shape<K, HV>::FIN_IT], int n,
+                                            int R, K kmin, int bl, unsigned char *region,
+                                            unsigned *wsum, unsigned *cmax, K *kd, K *vd,
+                                            unsigned &bad) {
+  using S = Shape<K, HV>;
+  constexpr int IB = HV ? FIN_IB : 0;
+  constexpr int FBM = fin_fb<K, HV, CT>();
+  constexpr int PERM = 1 << (FBM - 9);
+  static_assert(FBM >= 9 && NT == 512, "one bin per thread at least");
+  unsigned *bins = (unsigned *)region;  // thread t's run of bins at t (per + 1)
+  CT *pc = (CT *)(region + ((4 * ((1 << FBM) + NT) + 15) & ~15));
+  K *vst = (K *)((unsigned char *)pc + ((sizeof(CT) * S::FIN_CAP + 15) & ~15));
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int fb = min(max(bitlen64((uint64_t)(n - 1)) + 1, 9), FBM);
+  const int psh = fb - 9, per = 1 << psh;
+  const int bsh = (bl > fb ? bl - fb : 0) + IB;  // bin of a composite = c >> bsh
+  auto comp = [&](K k, int i) -> CT {
+    if constexpr (HV) return ((CT)(k - kmin) << IB) | (CT)i;
+    else return (CT)(k - kmin);
+  };
+  // values in input order; histogram of the bins
+#pragma unroll
+  for (int j = 0; j < S::FIN_IT; ++j) {
+    const int i = j * NT + threadIdx.x;
+    if (j < R && i < n) {
+      if constexpr (HV) vst[i] = rr[j].v;
+      const unsigned b = (unsigned)(comp(rr[j].k, i) >> bsh);
+      atomicAdd(&bins[b + (b >> psh)], 1u);
+    }
+  }
+  __syncthreads();
+  // thread t owns bins [t per, (t+1) per): bin starts = exclusive prefix
+  unsigned *mb = bins + threadIdx.x * (per + 1);
+  unsigned cnt[PERM];
+  unsigned sum = 0, mx = 0, multi = 0;
+#pragma unroll
+  for (int q = 0; q < PERM; ++q) {
+    cnt[q] = q < per ? mb[q] : 0u;
+    sum += cnt[q];
+    mx = max(mx, cnt[q]);
+    multi |= (cnt[q] > 1u ? 1u : 0u) << q;
+  }
+  unsigned x = sum;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  mx = __reduce_max_sync(0xffffffffu, mx);
+  if (lane == 31) wsum[w] = x;
+  if (lane == 0) atomicMax(cmax, mx);
+  __syncthreads();
+  if (*cmax > (unsigned)S::FIN_CMAX) return false;
+  unsigned run = x - sum;
+  for (int q = 0; q < w; ++q) run += wsum[q];
+  const unsigned my0 = run;
+#pragma unroll
+  for (int q = 0; q < PERM; ++q) {
+    if (q < per) mb[q] = run;
+    run += cnt[q];
+  }
+  __syncthreads();
+  // placement by bin; the bins then hold their ends
+#pragma unroll
+  for (int j = 0; j < S::FIN_IT; ++j) {
+    const int i = j * NT + threadIdx.x;
+    if (j < R && i < n) {
+      const CT c = comp(rr[j].k, i);
+      const unsigned b = (unsigned)(c >> bsh);
+      const unsigned p = atomicAdd(&bins[b + (b >> psh)], 1u);
+      if (p < (unsigned)n) pc[p] = c;
+      else bad = 1u + p;
+    }
+  }
+  __syncthreads();
+  // sort the own bins that hold more than one record
+  while (multi) {
+    const int q = __ffs(multi) - 1;
+    multi &= multi - 1u;
+    const unsigned s = q ? mb[q - 1] : my0;
+    const unsigned e = mb[q];
+    if (e > (unsigned)n || s >= e) {
+      bad = 1u + e;
+      continue;
+    }
+    for (unsigned a = s + 1; a < e; ++a) {
+      const CT v = pc[a];
+      unsigned b = a;
+      while (b > s) {
+        const CT u = pc[b - 1];
+        if (u <= v) break;
+        pc[b] = u;
+        --b;
+      }
+      pc[b] = v;
+    }
+  }
+  __syncthreads();
+  for (int p = threadIdx.x; p < n; p += NT) {
+    const CT c = pc[p];
+    kd[p] = kmin + (K)(c >> IB);
+    if constexpr (HV) vd[p] = vst[(unsigned)c & ((1u << IB) - 1u)];
+  }
+  return true;
+}
+
 template <typename K, bool HV>
 __device__ void phase_finish(const Params &P, int level, unsigned char *smem) {
   using S = Shape<K, HV>;
@@ -981,55 +1131,93 @@ __device__ void phase_finish(const Params &P, int level, unsigned char *smem) {
   const int64_t ntasks = min(ld_cg64(&c->ntasks), (long long)P.tmax);
   using RecT = Rec<K, HV>;
   Carve cv;
-  RecT *ra = cv.take<RecT>(S::FIN_CAP);
-  RecT *rb = cv.take<RecT>(S::FIN_CAP);
+  unsigned char *region = cv.take<unsigned char>(S::FIN_BYTES);
+  RecT *ra = (RecT *)region;  // LSD passes: two record buffers
+  RecT *rb = ra + S::FIN_CAP;
   uint16_t *wcnt = cv.take<uint16_t>(NWARP * FIN_NB);
   unsigned *dcnt = cv.take<unsigned>(FIN_NB);
   unsigned *doff = cv.take<unsigned>(FIN_NB);
   unsigned *sh = cv.take<unsigned>(NWARP + 1);
-  long long *task_sh = cv.take<long long>(1);
+  unsigned *wsum = cv.take<unsigned>(NWARP);
+  // per-task scalars, two copies: task k uses copy k & 1 while thread 0
+  // prepares the other for task k + 1
+  long long *task_sh = cv.take<long long>(2);
+  K *kmin_sh = cv.take<K>(2);
+  K *kmax_sh = cv.take<K>(2);
+  unsigned *cmax_sh = cv.take<unsigned>(2);
   int *flag_sh = cv.take<int>(1);
-  K *kmin_sh = cv.take<K>(1);
-  K *kmax_sh = cv.take<K>(1);
-  unsigned *cmax_sh = cv.take<unsigned>(1);
+  static_assert(2 * sizeof(RecT) * S::FIN_CAP <= (size_t)S::FIN_BYTES, "LSD buffers fit");
   static_assert(sizeof(RecT) * S::FIN_CAP >= 4 * NWARP * FIN_NB, "slots fit in a buffer");
-  static_assert(sizeof(RecT) * S::FIN_CAP >= 4 * S::FIN_NBW + (HV ? 2 * S::FIN_CAP : 0),
-                "bins and indices fit in a buffer");
-  static_assert(S::FIN_CAP < 65536, "indices fit in 16 bits");
-  static_assert(NT == 512 && S::FIN_FB >= 9, "bin runs");
-  unsigned *bins = (unsigned *)ra;                            // one-pass bins (padded)
-  uint16_t *ix = (uint16_t *)((unsigned char *)ra + 4 * S::FIN_NBW);  // original index
+  static_assert(S::FIN_CAP <= (1 << FIN_IB), "indices fit in FIN_IB bits");
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   uint16_t *mywc = wcnt + w * FIN_NB;
   long long my_recs = 0, my_tasks = 0, my_copy = 0, my_lsd = 0;
   unsigned bad = 0;  // self-check: a base-case slot out of range, reported once
+  // Tasks are claimed two ahead by thread 0: q1 = the next task (its id known,
+  // its records prefetched into L2 during this one), q2 = the one after (its
+  // claim in flight until the end of this task).
+  long long q1 = 0, q2 = 0;
+  long long dn_start = 0, dn_size = 0;  // thread 0: the next task's range
+  unsigned dn_src = 2;                  // and source buffer (2: none)
+  auto reset = [&](int q) {
+    kmin_sh[q] = (K)~(K)0;
+    kmax_sh[q] = (K)0;
+    cmax_sh[q] = 0u;
+  };
+  // thread 0, before the current task's last barrier: publish the next task
+  auto advance = [&](int q) {
+    task_sh[q] = q1;
+    reset(q);
+  };
+  auto prefetch_next = [&]() {
+    if (q1 < ntasks && dn_src <= 1u && dn_start >= 0 && dn_size > 0) {
+      const int64_t m = dn_size < S::FIN_CAP ? dn_size : S::FIN_CAP;
+      prefetch_l2<K>((const K *)P.keys[dn_src], dn_start, m, P.n);
+      if constexpr (HV) prefetch_l2<K>((const K *)P.vals[dn_src], dn_start, m, P.n);
+    }
+  };
+  int par = 0;
+  if (threadIdx.x == 0) {
+    task_sh[0] = atomic_add_ll(&c->task_ctr, 1ll);
+    q1 = atomic_add_ll(&c->task_ctr, 1ll);
+    reset(0);
+  }
+  __syncthreads();
   while (true) {
-    if (threadIdx.x == 0) {
-      *task_sh = atomic_add_ll(&c->task_ctr, 1ll);
-      *kmin_sh = (K)~(K)0;
-      *kmax_sh = (K)0;
-      *cmax_sh = 0u;
-    }
-    __syncthreads();
-    const int64_t ti = *task_sh;
-    __syncthreads();
+    const int64_t ti = task_sh[par];
     if (ti >= ntasks) break;
-    const Task tk = ldcg_obj(&P.tasks[ti]);
-    if (tk.src > 1 || tk.dst > 1 || tk.start < 0 || tk.size < 0 || tk.start + tk.size > P.n ||
-        (tk.kind != TASK_COPY && (tk.size > S::FIN_CAP || tk.hi < 0 || tk.hi > 64))) {
-      if (threadIdx.x == 0) check_failed(P, 6, ti, tk.size);
-      continue;
+    if (threadIdx.x == 0) {
+      q2 = atomic_add_ll(&c->task_ctr, 1ll);
+      if (q1 < ntasks) {
+        const Task *d = &P.tasks[q1];
+        dn_start = ld_cg64((const long long *)&d->start);
+        dn_size = ld_cg64((const long long *)&d->size);
+        dn_src = (unsigned)__ldcg((const unsigned char *)&d->src);
+      }
     }
+    const Task tk = ldcg_obj(&P.tasks[ti]);
+    const bool ok = !(tk.src > 1 || tk.dst > 1 || tk.start < 0 || tk.size < 0 ||
+                      tk.start + tk.size > P.n ||
+                      (tk.kind != TASK_COPY && (tk.size > S::FIN_CAP || tk.hi < 0 || tk.hi > 64)));
     const K *ksrc = (const K *)P.keys[tk.src];
     K *kdst = (K *)P.keys[tk.dst];
     const K *vsrc = HV ? (const K *)P.vals[tk.src] : nullptr;
     K *vdst = HV ? (K *)P.vals[tk.dst] : nullptr;
-    if (tk.kind == TASK_COPY) {
-      for (int64_t i = threadIdx.x; i < tk.size; i += NT) {
-        kdst[tk.start + i] = ld_key<K>(ksrc + tk.start + i);
-        if constexpr (HV) vdst[tk.start + i] = ld_key<K>(vsrc + tk.start + i);
+    if (!ok || tk.kind == TASK_COPY) {
+      if (threadIdx.x == 0) {
+        advance(par ^ 1);
+        if (!ok) check_failed(P, 6, ti, tk.size);
       }
-      my_copy += tk.size;
+      if (ok) {
+        for (int64_t i = threadIdx.x; i < tk.size; i += NT) {
+          kdst[tk.start + i] = ld_key<K>(ksrc + tk.start + i);
+          if constexpr (HV) vdst[tk.start + i] = ld_key<K>(vsrc + tk.start + i);
+        }
+        my_copy += tk.size;
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) q1 = q2;
+      par ^= 1;
       continue;
     }
     const int n = (int)tk.size;
@@ -1060,16 +1248,27 @@ __device__ void phase_finish(const Params &P, int level, unsigned char *smem) {
     kmx = warp_max(kmx);
     if (lane == 0) {
       if constexpr (sizeof(K) == 4) {
-        atomicMin((unsigned *)kmin_sh, (unsigned)kmn);
-        atomicMax((unsigned *)kmax_sh, (unsigned)kmx);
+        atomicMin((unsigned *)&kmin_sh[par], (unsigned)kmn);
+        atomicMax((unsigned *)&kmax_sh[par], (unsigned)kmx);
       } else {
-        atomicMin((unsigned long long *)kmin_sh, (unsigned long long)kmn);
-        atomicMax((unsigned long long *)kmax_sh, (unsigned long long)kmx);
+        atomicMin((unsigned long long *)&kmin_sh[par], (unsigned long long)kmn);
+        atomicMax((unsigned long long *)&kmax_sh[par], (unsigned long long)kmx);
       }
     }
+    {
+      // zero the one-pass bins (the widest layout either composite uses)
+      const int fbz = min(max(bitlen64((uint64_t)(n - 1)) + 1, 9), fin_fb<K, HV, uint32_t>());
+      uint4 *z = (uint4 *)region;
+      const int nw = ((1 << fbz) + NT) / 4;
+      for (int i = threadIdx.x; i < nw; i += NT) z[i] = make_uint4(0, 0, 0, 0);
+    }
     __syncthreads();
-    const K kmin = *kmin_sh;
-    const uint64_t span = (uint64_t)(*kmax_sh) - (uint64_t)kmin;
+    if (threadIdx.x == 0) {
+      advance(par ^ 1);
+      prefetch_next();
+    }
+    const K kmin = kmin_sh[par];
+    const uint64_t span = (uint64_t)kmax_sh[par] - (uint64_t)kmin;
     if (span == 0) {  // one key: the stable order is the input order
 #pragma unroll
       for (int j = 0; j < S::FIN_IT; ++j) {
@@ -1080,102 +1279,28 @@ __device__ void phase_finish(const Params &P, int level, unsigned char *smem) {
         }
       }
       __syncthreads();
+      if (threadIdx.x == 0) q1 = q2;
+      par ^= 1;
       continue;
     }
-    // one counting pass on the top fb bits of key - kmin (2^fb bins, 2n to
-    // 4n of them where shared memory allows: fewer records share a bin, so
-    // the in-bin ranking below rarely loops): histogram, bin starts,
-    // placement in arbitrary order inside a bin; the write-out then ranks
-    // each record among its bin's records by (key, original index), which
-    // gives the stable order
-    const int fb = min(max(bitlen64((uint64_t)(n - 1)) + 1, 9), S::FIN_FB);
-    const int psh = fb - 9;                 // log2 bins per thread
-    const int per = 1 << psh;
-    const int bsh = bitlen64(span) > fb ? bitlen64(span) - fb : 0;
-    // bin of a key (32-bit arithmetic for 32-bit keys)
-    auto bin_of = [&](K k) -> unsigned {
-      if constexpr (sizeof(K) == 4) return (unsigned)(k - kmin) >> bsh;
-      else return (unsigned)((uint64_t)(k - kmin) >> bsh);
-    };
-    {
-      uint4 *z = (uint4 *)bins;
-      const int nw = ((1 << fb) + NT) / 4;
-      for (int i = threadIdx.x; i < nw; i += NT) z[i] = make_uint4(0, 0, 0, 0);
-    }
-    __syncthreads();
-#pragma unroll
-    for (int j = 0; j < S::FIN_IT; ++j) {
-      const int i = j * NT + threadIdx.x;
-      if (j < R && i < n) {
-        const unsigned b = bin_of(rr[j].k);
-        atomicAdd(&bins[b + (b >> psh)], 1u);
+    const int bl = bitlen64(span);
+    constexpr int IB = HV ? FIN_IB : 0;
+    bool done = false;
+    if (bl + IB <= 32) {
+      done = fin_onepass<K, HV, uint32_t>(rr, n, R, kmin, bl, region, wsum, &cmax_sh[par], kd,
+                                          vd, bad);
+    } else {
+      if constexpr (sizeof(K) == 8 || HV) {
+        if (bl + IB <= 64)
+          done = fin_onepass<K, HV, uint64_t>(rr, n, R, kmin, bl, region, wsum, &cmax_sh[par],
+                                              kd, vd, bad);
       }
     }
-    __syncthreads();
-    {
-      // thread t owns bins [t per, (t+1) per), stored at t (per + 1)
-      unsigned *mb = bins + threadIdx.x * (per + 1);
-      unsigned cnt[S::FIN_PER];
-      unsigned sum = 0, mx = 0;
-#pragma unroll
-      for (int q = 0; q < S::FIN_PER; ++q) {
-        cnt[q] = q < per ? mb[q] : 0u;
-        sum += cnt[q];
-        mx = max(mx, cnt[q]);
-      }
-      mx = __reduce_max_sync(0xffffffffu, mx);
-      if (lane == 0) atomicMax(cmax_sh, mx);
-      unsigned tot;
-      unsigned run = block_excl_scan<unsigned>(sum, sh, tot);
-#pragma unroll
-      for (int q = 0; q < S::FIN_PER; ++q) {
-        if (q < per) mb[q] = run;
-        run += cnt[q];
-      }
-    }
-    __syncthreads();
-    if (*cmax_sh <= (unsigned)S::FIN_CMAX) {
-#pragma unroll
-      for (int j = 0; j < S::FIN_IT; ++j) {
-        const int i = j * NT + threadIdx.x;
-        if (j < R && i < n) {
-          const unsigned b = bin_of(rr[j].k);
-          const unsigned p = atomicAdd(&bins[b + (b >> psh)], 1u);
-          rb[p] = rr[j];
-          if constexpr (HV) ix[p] = (uint16_t)i;
-        }
-      }
-      __syncthreads();
-      // bins now hold their ends: bin b is [end(b-1), end(b))
-      for (int p = threadIdx.x; p < n; p += NT) {
-        const RecT x = rb[p];
-        const unsigned b = bin_of(x.k);
-        const unsigned e0 = bins[b + (b >> psh)];
-        const unsigned s0 = b ? bins[(b - 1) + ((b - 1) >> psh)] : 0u;
-        unsigned r = (unsigned)p;
-        if (e0 - s0 > 1) {
-          r = s0;
-          if constexpr (HV) {
-            const uint16_t xi = ix[p];
-            for (unsigned q = s0; q < e0; ++q) {
-              const K y = rb[q].k;
-              r += (y < x.k || (y == x.k && ix[q] < xi)) ? 1u : 0u;
-            }
-          } else {
-            for (unsigned q = s0; q < e0; ++q) {
-              const K y = rb[q].k;
-              r += (y < x.k || (y == x.k && q < (unsigned)p)) ? 1u : 0u;
-            }
-          }
-        }
-        kd[r] = x.k;
-        if constexpr (HV) vd[r] = x.v;
-      }
-      __syncthreads();
-      continue;
-    }
-    // a bin with many equal-prefix keys: stable LSD passes over the task's
-    // hi bits (the bins are no longer read)
+    if (threadIdx.x == 0) q1 = q2;
+    par ^= 1;
+    if (done) continue;
+    // a bin with many equal-prefix keys (or a key range too wide for a
+    // composite): stable LSD passes over the task's hi bits
     my_lsd += 1;
 #pragma unroll
     for (int j = 0; j < S::FIN_IT; ++j) {
