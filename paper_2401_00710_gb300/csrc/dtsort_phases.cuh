@@ -82,7 +82,7 @@ constexpr size_t smem_bytes() {
   fin += 16 + (size_t)S::FIN_BYTES;
   fin += 16 + 2 * (size_t)NWARP * FIN_NB;
   fin += 16 + 4 * FIN_NB * 2;
-  fin += 16 + 4 * (NWARP + 1) + 16 + 4 * NWARP + 4 * 16 + 256;
+  fin += 16 + 4 * (NWARP + 1) + 16 + 4 * NWARP + 4 * 16 + 16 + 256;
   // sampler
   size_t smp = 16 + sizeof(K) * SMAX + 16 + sizeof(K) * (SMAX / 2 + 8) + 16 + 4 * 1024 +
                16 + sizeof(K) * HASH_HW + 16 + 2 * HASH_HW + 512;
@@ -1003,52 +1003,70 @@ __host__ __device__ constexpr int fin_fb() {
   return fb;
 }
 
-// One-pass base case of a task of n <= FIN_CAP records held in registers
-// (item j of thread t is record i = j NT + t), keys in [kmin, kmin + 2^bl).
-// Each record becomes the composite c = (key - kmin) << FIN_IB | i (without
-// values c = key - kmin).  With values the composites are distinct and their
-// order is the order of (key, original index), i.e. the stable order.  A
-// counting pass on the top fb bits of key - kmin places the composites by bin
-// (in arbitrary order inside a bin); the thread that owns a run of bins then
-// sorts each of its bins that holds more than one record (insertion sort:
-// bins hold about half a record on average), and the write-out is a plain
-// coalesced copy of the placed order, the value taken from the input-order
-// copy by the composite's index.  The caller has zeroed the bins and holds
-// barrier-separated parity copies of the shared scalars.  Returns false,
-// having written nothing to global memory, when a bin holds more than
-// FIN_CMAX records.
+// Layout of the base-case area for composites of type CT: the bins (thread
+// t's run of per bins at t (per + 1)), the placed composites, the values in
+// input order.
 template <typename K, bool HV, typename CT>
-__device__ __forceinline__ bool fin_onepass(const Rec<K, HV> (&rr)[Shape<K, HV>::FIN_IT], int n,
-                                            int R, K kmin, int bl, unsigned char *region,
-                                            unsigned *wsum, unsigned *cmax, K *kd, K *vd,
-                                            unsigned &bad) {
+struct FinArea {
+  static constexpr int FBM = fin_fb<K, HV, CT>();
+  static constexpr int PC_OFF = (4 * ((1 << FBM) + NT) + 15) & ~15;
+  static constexpr int V_OFF = PC_OFF + ((int)((sizeof(CT) * Shape<K, HV>::FIN_CAP + 15) & ~15));
+};
+
+// Histogram of a task's records (item j of thread t is record i = j NT + t,
+// keys in [kb, kb + 2^bits)) on bins = (key - kb) >> bsh, and the values in
+// input order; the bins must be zero.
+template <typename K, bool HV, typename CT>
+__device__ __forceinline__ void fin_hist(const Rec<K, HV> (&rr)[Shape<K, HV>::FIN_IT], int n,
+                                         int R, K kb, int bsh, int psh, unsigned char *region) {
   using S = Shape<K, HV>;
-  constexpr int IB = HV ? FIN_IB : 0;
-  constexpr int FBM = fin_fb<K, HV, CT>();
-  constexpr int PERM = 1 << (FBM - 9);
-  static_assert(FBM >= 9 && NT == 512, "one bin per thread at least");
-  unsigned *bins = (unsigned *)region;  // thread t's run of bins at t (per + 1)
-  CT *pc = (CT *)(region + ((4 * ((1 << FBM) + NT) + 15) & ~15));
-  K *vst = (K *)((unsigned char *)pc + ((sizeof(CT) * S::FIN_CAP + 15) & ~15));
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int fb = min(max(bitlen64((uint64_t)(n - 1)) + 1, 9), FBM);
-  const int psh = fb - 9, per = 1 << psh;
-  const int bsh = (bl > fb ? bl - fb : 0) + IB;  // bin of a composite = c >> bsh
-  auto comp = [&](K k, int i) -> CT {
-    if constexpr (HV) return ((CT)(k - kmin) << IB) | (CT)i;
-    else return (CT)(k - kmin);
-  };
-  // values in input order; histogram of the bins
+  using A = FinArea<K, HV, CT>;
+  unsigned *bins = (unsigned *)region;
+  K *vst = (K *)(region + A::V_OFF);
 #pragma unroll
   for (int j = 0; j < S::FIN_IT; ++j) {
     const int i = j * NT + threadIdx.x;
     if (j < R && i < n) {
       if constexpr (HV) vst[i] = rr[j].v;
-      const unsigned b = (unsigned)(comp(rr[j].k, i) >> bsh);
+      const unsigned b = (unsigned)((uint64_t)(K)(rr[j].k - kb) >> bsh);
       atomicAdd(&bins[b + (b >> psh)], 1u);
     }
   }
-  __syncthreads();
+}
+
+// One-pass base case of a task of n <= FIN_CAP records held in registers
+// (item j of thread t is record i = j NT + t), keys in [kb, kb + 2^bits),
+// after fin_hist has counted its 2^fb bins (bin = (key - kb) >> bsh).  Each
+// record is the composite c = (key - kb) << FIN_IB | i (without values
+// c = key - kb): with values the composites are distinct and their order is
+// the order of (key, original index), i.e. the stable order.  The bins'
+// counts give their starts; the composites are placed by bin (in arbitrary
+// order inside a bin); the thread that owns a run of bins then sorts each of
+// its bins that holds more than one record (insertion sort: bins hold about
+// half a record on average), and the write-out is a plain coalesced copy of
+// the placed order, the value taken from the input-order copy by the
+// composite's index.  Returns false, having written nothing to global
+// memory, when a bin holds more than FIN_CMAX records.  Barriers: 4 (1 when
+// it returns false).
+template <typename K, bool HV, typename CT>
+__device__ __forceinline__ bool fin_core(const Rec<K, HV> (&rr)[Shape<K, HV>::FIN_IT], int n,
+                                         int R, K kb, int fb, int bsh, unsigned char *region,
+                                         unsigned *wsum, unsigned *cmax, K *kd, K *vd,
+                                         unsigned &bad) {
+  using S = Shape<K, HV>;
+  using A = FinArea<K, HV, CT>;
+  constexpr int IB = HV ? FIN_IB : 0;
+  constexpr int PERM = 1 << (A::FBM - 9);
+  static_assert(A::FBM >= 9 && NT == 512, "one bin per thread at least");
+  unsigned *bins = (unsigned *)region;
+  CT *pc = (CT *)(region + A::PC_OFF);
+  const K *vst = (const K *)(region + A::V_OFF);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int psh = fb - 9, per = 1 << psh;
+  auto comp = [&](K k, int i) -> CT {
+    if constexpr (HV) return ((CT)(K)(k - kb) << IB) | (CT)i;
+    else return (CT)(K)(k - kb);
+  };
   // thread t owns bins [t per, (t+1) per): bin starts = exclusive prefix
   unsigned *mb = bins + threadIdx.x * (per + 1);
   unsigned cnt[PERM];
@@ -1085,10 +1103,9 @@ __device__ __forceinline__ bool fin_onepass(const Rec<K, HV> (&rr)[Shape<K, HV>:
   for (int j = 0; j < S::FIN_IT; ++j) {
     const int i = j * NT + threadIdx.x;
     if (j < R && i < n) {
-      const CT c = comp(rr[j].k, i);
-      const unsigned b = (unsigned)(c >> bsh);
+      const unsigned b = (unsigned)((uint64_t)(K)(rr[j].k - kb) >> bsh);
       const unsigned p = atomicAdd(&bins[b + (b >> psh)], 1u);
-      if (p < (unsigned)n) pc[p] = c;
+      if (p < (unsigned)n) pc[p] = comp(rr[j].k, i);
       else bad = 1u + p;
     }
   }
@@ -1118,7 +1135,7 @@ __device__ __forceinline__ bool fin_onepass(const Rec<K, HV> (&rr)[Shape<K, HV>:
   __syncthreads();
   for (int p = threadIdx.x; p < n; p += NT) {
     const CT c = pc[p];
-    kd[p] = kmin + (K)(c >> IB);
+    kd[p] = kb + (K)(c >> IB);
     if constexpr (HV) vd[p] = vst[(unsigned)c & ((1u << IB) - 1u)];
   }
   return true;
@@ -1140,19 +1157,29 @@ __device__ void phase_finish(const Params &P, int level, unsigned char *smem) {
   unsigned *sh = cv.take<unsigned>(NWARP + 1);
   unsigned *wsum = cv.take<unsigned>(NWARP);
   // per-task scalars, two copies: task k uses copy k & 1 while thread 0
-  // prepares the other for task k + 1
+  // prepares the other for task k + 1; cmax_sh[2]: the min/max path's own
   long long *task_sh = cv.take<long long>(2);
   K *kmin_sh = cv.take<K>(2);
   K *kmax_sh = cv.take<K>(2);
-  unsigned *cmax_sh = cv.take<unsigned>(2);
+  unsigned *cmax_sh = cv.take<unsigned>(3);
   int *flag_sh = cv.take<int>(1);
   static_assert(2 * sizeof(RecT) * S::FIN_CAP <= (size_t)S::FIN_BYTES, "LSD buffers fit");
   static_assert(sizeof(RecT) * S::FIN_CAP >= 4 * NWARP * FIN_NB, "slots fit in a buffer");
   static_assert(S::FIN_CAP <= (1 << FIN_IB), "indices fit in FIN_IB bits");
+  constexpr int IB = HV ? FIN_IB : 0;
+  constexpr bool WIDE = sizeof(K) == 8 || HV;  // 64-bit composites can be needed
+  constexpr int FBM32 = FinArea<K, HV, uint32_t>::FBM;
+  constexpr int FBM64 = FinArea<K, HV, uint64_t>::FBM;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   uint16_t *mywc = wcnt + w * FIN_NB;
   long long my_recs = 0, my_tasks = 0, my_copy = 0, my_lsd = 0;
   unsigned bad = 0;  // self-check: a base-case slot out of range, reported once
+  // every bin of the widest layout starts at zero for every task (cleared
+  // again at the end of each task that used them)
+  auto zero_bins = [&]() {
+    uint4 *z = (uint4 *)region;
+    for (int i = threadIdx.x; i < ((1 << FBM32) + NT) / 4; i += NT) z[i] = make_uint4(0, 0, 0, 0);
+  };
   // Tasks are claimed two ahead by thread 0: q1 = the next task (its id known,
   // its records prefetched into L2 during this one), q2 = the one after (its
   // claim in flight until the end of this task).
@@ -1177,6 +1204,7 @@ __device__ void phase_finish(const Params &P, int level, unsigned char *smem) {
     }
   };
   int par = 0;
+  zero_bins();
   if (threadIdx.x == 0) {
     task_sh[0] = atomic_add_ll(&c->task_ctr, 1ll);
     q1 = atomic_add_ll(&c->task_ctr, 1ll);
@@ -1223,15 +1251,24 @@ __device__ void phase_finish(const Params &P, int level, unsigned char *smem) {
     const int n = (int)tk.size;
     my_recs += n;
     my_tasks += 1;
-    // records in registers (item j of thread t is record j * NT + t), and
-    // the task's key range
     const int R = (n + NT - 1) / NT;  // rounds with live items (same for all threads)
     const K *ks = ksrc + tk.start;
     const K *vs = HV ? vsrc + tk.start : nullptr;
     K *kd = kdst + tk.start;
     K *vd = HV ? vdst + tk.start : nullptr;
+    // composites over the task's own key range [base, base + 2^hi) when they
+    // fit; the bins are counted while the records are loaded into registers
+    // (item j of thread t is record j * NT + t)
+    const int hi = tk.hi;
+    const int ct = hi + IB <= 32 ? 1 : (WIDE && hi + IB <= 64 ? 2 : 0);
+    const int fb0 = min(max(bitlen64((uint64_t)(n - 1)) + 1, 9), ct == 2 ? FBM64 : FBM32);
+    const int bsh0 = hi > fb0 ? hi - fb0 : 0;
+    const int psh0 = fb0 - 9;
+    const K kb0 = (K)tk.base;
+    unsigned *bins = (unsigned *)region;
+    K *vst0 = (K *)(region + (ct == 2 ? FinArea<K, HV, uint64_t>::V_OFF
+                                      : FinArea<K, HV, uint32_t>::V_OFF));
     RecT rr[S::FIN_IT];
-    K kmn = (K)~(K)0, kmx = (K)0;
 #pragma unroll
     for (int j = 0; j < S::FIN_IT; ++j) {
       if (j < R) {
@@ -1239,151 +1276,192 @@ __device__ void phase_finish(const Params &P, int level, unsigned char *smem) {
         if (i < n) {
           rr[j].k = ld_key<K>(ks + i);
           if constexpr (HV) rr[j].v = ld_key<K>(vs + i);
-          kmn = rr[j].k < kmn ? rr[j].k : kmn;
-          kmx = rr[j].k > kmx ? rr[j].k : kmx;
         }
       }
     }
-    kmn = warp_min(kmn);
-    kmx = warp_max(kmx);
-    if (lane == 0) {
-      if constexpr (sizeof(K) == 4) {
-        atomicMin((unsigned *)&kmin_sh[par], (unsigned)kmn);
-        atomicMax((unsigned *)&kmax_sh[par], (unsigned)kmx);
-      } else {
-        atomicMin((unsigned long long *)&kmin_sh[par], (unsigned long long)kmn);
-        atomicMax((unsigned long long *)&kmax_sh[par], (unsigned long long)kmx);
+    if (ct) {
+#pragma unroll
+      for (int j = 0; j < S::FIN_IT; ++j) {
+        const int i = j * NT + threadIdx.x;
+        if (j < R && i < n) {
+          const uint64_t dk = (uint64_t)(K)(rr[j].k - kb0);
+          if (hi < 64 && (dk >> hi) != 0) {
+            bad = 1u + (unsigned)i;  // a key outside the task's range
+          } else {
+            if constexpr (HV) vst0[i] = rr[j].v;
+            const unsigned b = (unsigned)(dk >> bsh0);
+            atomicAdd(&bins[b + (b >> psh0)], 1u);
+          }
+        }
       }
-    }
-    {
-      // zero the one-pass bins (the widest layout either composite uses)
-      const int fbz = min(max(bitlen64((uint64_t)(n - 1)) + 1, 9), fin_fb<K, HV, uint32_t>());
-      uint4 *z = (uint4 *)region;
-      const int nw = ((1 << fbz) + NT) / 4;
-      for (int i = threadIdx.x; i < nw; i += NT) z[i] = make_uint4(0, 0, 0, 0);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
       advance(par ^ 1);
       prefetch_next();
     }
-    const K kmin = kmin_sh[par];
-    const uint64_t span = (uint64_t)kmax_sh[par] - (uint64_t)kmin;
-    if (span == 0) {  // one key: the stable order is the input order
+    bool done = false;
+    bool wide = false;  // 64-bit composites: they overlap the widest bin layout
+    if (ct == 1) {
+      done = fin_core<K, HV, uint32_t>(rr, n, R, kb0, fb0, bsh0, region, wsum, &cmax_sh[par], kd,
+                                       vd, bad);
+    } else if (ct == 2) {
+      if constexpr (WIDE)
+        done = wide = fin_core<K, HV, uint64_t>(rr, n, R, kb0, fb0, bsh0, region, wsum,
+                                                &cmax_sh[par], kd, vd, bad);
+    }
+    if (!done) {
+      // keys clustered inside the task's range (a bin of more than FIN_CMAX
+      // records), or a range too wide: bins over [min, max] of the keys
+      K kmn = (K)~(K)0, kmx = (K)0;
 #pragma unroll
       for (int j = 0; j < S::FIN_IT; ++j) {
         const int i = j * NT + threadIdx.x;
         if (j < R && i < n) {
-          kd[i] = rr[j].k;
-          if constexpr (HV) vd[i] = rr[j].v;
+          kmn = rr[j].k < kmn ? rr[j].k : kmn;
+          kmx = rr[j].k > kmx ? rr[j].k : kmx;
         }
       }
+      kmn = warp_min(kmn);
+      kmx = warp_max(kmx);
+      if (lane == 0) {
+        if constexpr (sizeof(K) == 4) {
+          atomicMin((unsigned *)&kmin_sh[par], (unsigned)kmn);
+          atomicMax((unsigned *)&kmax_sh[par], (unsigned)kmx);
+        } else {
+          atomicMin((unsigned long long *)&kmin_sh[par], (unsigned long long)kmn);
+          atomicMax((unsigned long long *)&kmax_sh[par], (unsigned long long)kmx);
+        }
+      }
+      if (threadIdx.x == 0) cmax_sh[2] = 0u;
+      zero_bins();
       __syncthreads();
-      if (threadIdx.x == 0) q1 = q2;
-      par ^= 1;
-      continue;
-    }
-    const int bl = bitlen64(span);
-    constexpr int IB = HV ? FIN_IB : 0;
-    bool done = false;
-    if (bl + IB <= 32) {
-      done = fin_onepass<K, HV, uint32_t>(rr, n, R, kmin, bl, region, wsum, &cmax_sh[par], kd,
-                                          vd, bad);
-    } else {
-      if constexpr (sizeof(K) == 8 || HV) {
-        if (bl + IB <= 64)
-          done = fin_onepass<K, HV, uint64_t>(rr, n, R, kmin, bl, region, wsum, &cmax_sh[par],
-                                              kd, vd, bad);
+      const K kmin = kmin_sh[par];
+      const uint64_t span = (uint64_t)kmax_sh[par] - (uint64_t)kmin;
+      if (span == 0) {  // one key: the stable order is the input order
+#pragma unroll
+        for (int j = 0; j < S::FIN_IT; ++j) {
+          const int i = j * NT + threadIdx.x;
+          if (j < R && i < n) {
+            kd[i] = rr[j].k;
+            if constexpr (HV) vd[i] = rr[j].v;
+          }
+        }
+        done = true;
+      } else {
+        const int bl = bitlen64(span);
+        const int ct1 = bl + IB <= 32 ? 1 : (WIDE && bl + IB <= 64 ? 2 : 0);
+        const int fb1 = min(max(bitlen64((uint64_t)(n - 1)) + 1, 9), ct1 == 2 ? FBM64 : FBM32);
+        const int bsh1 = bl > fb1 ? bl - fb1 : 0;
+        if (ct1 == 1) {
+          fin_hist<K, HV, uint32_t>(rr, n, R, kmin, bsh1, fb1 - 9, region);
+          __syncthreads();
+          done = fin_core<K, HV, uint32_t>(rr, n, R, kmin, fb1, bsh1, region, wsum, &cmax_sh[2],
+                                           kd, vd, bad);
+        } else if (ct1 == 2) {
+          if constexpr (WIDE) {
+            fin_hist<K, HV, uint64_t>(rr, n, R, kmin, bsh1, fb1 - 9, region);
+            __syncthreads();
+            done = wide = fin_core<K, HV, uint64_t>(rr, n, R, kmin, fb1, bsh1, region, wsum,
+                                                    &cmax_sh[2], kd, vd, bad);
+          }
+        }
       }
     }
+    if (!done) {
+      // a bin with many equal-prefix keys: stable LSD passes over the task's
+      // hi bits
+      my_lsd += 1;
+#pragma unroll
+      for (int j = 0; j < S::FIN_IT; ++j) {
+        const int i = j * NT + threadIdx.x;
+        if (j < R && i < n) ra[i] = rr[j];
+      }
+      __syncthreads();
+      RecT *rin = ra, *rout = rb;
+      const int passes = (tk.hi + FIN_DIG - 1) / FIN_DIG;
+      // every warp ranks R consecutive rounds of 32 items (warp w covers
+      // [32 R w, 32 R (w+1)) of the current order), R as small as n allows
+      for (int q = 0; q < passes; ++q) {
+        const int shift = q * FIN_DIG;
+        const int bits = tk.hi - shift < FIN_DIG ? tk.hi - shift : FIN_DIG;
+        const unsigned dmask = (1u << bits) - 1u;
+        unsigned *fslots = (unsigned *)rout;  // rout is free until the scatter
+        {
+          uint4 *z = (uint4 *)wcnt;
+          for (int i = threadIdx.x; i < NWARP * FIN_NB * 2 / 16; i += NT) z[i] = make_uint4(0, 0, 0, 0);
+          uint4 *z2 = (uint4 *)fslots;
+          for (int i = threadIdx.x; i < NWARP * FIN_NB * 4 / 16; i += NT) z2[i] = make_uint4(0, 0, 0, 0);
+        }
+        __syncthreads();
+        unsigned *myfs = fslots + w * FIN_NB;
+        unsigned dr[S::FIN_IT];
+#pragma unroll
+        for (int j = 0; j < S::FIN_IT; ++j) {
+          const int i = w * 32 * R + j * 32 + lane;
+          dr[j] = 0xFFFFFFFFu;
+          if (j < R && w * 32 * R + j * 32 < n) {  // warp-uniform
+            unsigned d = 1u << FIN_DIG;  // dummy digit
+            if (i < n) d = (unsigned)(((uint64_t)rin[i].k - tk.base) >> shift) & dmask;
+            const unsigned r = warp_rank_slots(d, myfs, mywc);
+            dr[j] = (d << 16) | r;
+          }
+        }
+        __syncthreads();
+        if (threadIdx.x < (1 << FIN_DIG)) {
+          const int d = threadIdx.x;
+          unsigned run = 0;
+#pragma unroll
+          for (int qq = 0; qq < NWARP; ++qq) {
+            const unsigned x = wcnt[qq * FIN_NB + d];
+            wcnt[qq * FIN_NB + d] = (uint16_t)run;
+            run += x;
+          }
+          dcnt[d] = run;
+        }
+        if (threadIdx.x == 0) *flag_sh = 0;
+        __syncthreads();
+        {
+          const unsigned v = threadIdx.x < (1 << FIN_DIG) ? dcnt[threadIdx.x] : 0u;
+          if (v == (unsigned)n) *flag_sh = 1;  // one digit holds everything
+          unsigned tot;
+          const unsigned o = block_excl_scan<unsigned>(v, sh, tot);
+          if (threadIdx.x < (1 << FIN_DIG)) doff[threadIdx.x] = o;
+        }
+        __syncthreads();
+        if (*flag_sh) continue;  // pass would be the identity
+#pragma unroll
+        for (int j = 0; j < S::FIN_IT; ++j) {
+          const int i = w * 32 * R + j * 32 + lane;
+          if (j < R && i < n) {
+            const unsigned d = dr[j] >> 16;
+            const unsigned pp = doff[d] + wcnt[w * FIN_NB + d] + (dr[j] & 0xFFFFu);
+            if (d >= (1u << FIN_DIG) || pp >= (unsigned)n) {
+              bad = 1u + pp;
+              continue;
+            }
+            rout[pp] = rin[i];
+          }
+        }
+        __syncthreads();
+        RecT *t_ = rin;
+        rin = rout;
+        rout = t_;
+      }
+      for (int i = threadIdx.x; i < n; i += NT) {
+        const RecT x = rin[i];
+        kdst[tk.start + i] = x.k;
+        if constexpr (HV) vdst[tk.start + i] = x.v;
+      }
+      __syncthreads();
+    }
+    // clear the bins for the next task once no thread reads this task's
+    // composites where they overlap them
+    if (wide) __syncthreads();
+    zero_bins();
+    __syncthreads();
     if (threadIdx.x == 0) q1 = q2;
     par ^= 1;
-    if (done) continue;
-    // a bin with many equal-prefix keys (or a key range too wide for a
-    // composite): stable LSD passes over the task's hi bits
-    my_lsd += 1;
-#pragma unroll
-    for (int j = 0; j < S::FIN_IT; ++j) {
-      const int i = j * NT + threadIdx.x;
-      if (j < R && i < n) ra[i] = rr[j];
-    }
-    __syncthreads();
-    RecT *rin = ra, *rout = rb;
-    const int passes = (tk.hi + FIN_DIG - 1) / FIN_DIG;
-    // every warp ranks R consecutive rounds of 32 items (warp w covers
-    // [32 R w, 32 R (w+1)) of the current order), R as small as n allows
-    for (int q = 0; q < passes; ++q) {
-      const int shift = q * FIN_DIG;
-      const int bits = tk.hi - shift < FIN_DIG ? tk.hi - shift : FIN_DIG;
-      const unsigned dmask = (1u << bits) - 1u;
-      unsigned *fslots = (unsigned *)rout;  // rout is free until the scatter
-      {
-        uint4 *z = (uint4 *)wcnt;
-        for (int i = threadIdx.x; i < NWARP * FIN_NB * 2 / 16; i += NT) z[i] = make_uint4(0, 0, 0, 0);
-        uint4 *z2 = (uint4 *)fslots;
-        for (int i = threadIdx.x; i < NWARP * FIN_NB * 4 / 16; i += NT) z2[i] = make_uint4(0, 0, 0, 0);
-      }
-      __syncthreads();
-      unsigned *myfs = fslots + w * FIN_NB;
-      unsigned dr[S::FIN_IT];
-#pragma unroll
-      for (int j = 0; j < S::FIN_IT; ++j) {
-        const int i = w * 32 * R + j * 32 + lane;
-        dr[j] = 0xFFFFFFFFu;
-        if (j < R && w * 32 * R + j * 32 < n) {  // warp-uniform
-          unsigned d = 1u << FIN_DIG;  // dummy digit
-          if (i < n) d = (unsigned)(((uint64_t)rin[i].k - tk.base) >> shift) & dmask;
-          const unsigned r = warp_rank_slots(d, myfs, mywc);
-          dr[j] = (d << 16) | r;
-        }
-      }
-      __syncthreads();
-      if (threadIdx.x < (1 << FIN_DIG)) {
-        const int d = threadIdx.x;
-        unsigned run = 0;
-#pragma unroll
-        for (int qq = 0; qq < NWARP; ++qq) {
-          const unsigned x = wcnt[qq * FIN_NB + d];
-          wcnt[qq * FIN_NB + d] = (uint16_t)run;
-          run += x;
-        }
-        dcnt[d] = run;
-      }
-      if (threadIdx.x == 0) *flag_sh = 0;
-      __syncthreads();
-      {
-        const unsigned v = threadIdx.x < (1 << FIN_DIG) ? dcnt[threadIdx.x] : 0u;
-        if (v == (unsigned)n) *flag_sh = 1;  // one digit holds everything
-        unsigned tot;
-        const unsigned o = block_excl_scan<unsigned>(v, sh, tot);
-        if (threadIdx.x < (1 << FIN_DIG)) doff[threadIdx.x] = o;
-      }
-      __syncthreads();
-      if (*flag_sh) continue;  // pass would be the identity
-#pragma unroll
-      for (int j = 0; j < S::FIN_IT; ++j) {
-        const int i = w * 32 * R + j * 32 + lane;
-        if (j < R && i < n) {
-          const unsigned d = dr[j] >> 16;
-          const unsigned pp = doff[d] + wcnt[w * FIN_NB + d] + (dr[j] & 0xFFFFu);
-          if (d >= (1u << FIN_DIG) || pp >= (unsigned)n) {
-            bad = 1u + pp;
-            continue;
-          }
-          rout[pp] = rin[i];
-        }
-      }
-      __syncthreads();
-      RecT *t_ = rin;
-      rin = rout;
-      rout = t_;
-    }
-    for (int i = threadIdx.x; i < n; i += NT) {
-      const RecT x = rin[i];
-      kdst[tk.start + i] = x.k;
-      if constexpr (HV) vdst[tk.start + i] = x.v;
-    }
-    __syncthreads();
   }
   if (threadIdx.x == 0) {
     if (my_tasks) atomic_add_ll(&c->st_fin_tasks, my_tasks);
