@@ -829,12 +829,21 @@ __device__ void phase_scatter(const Params &P, int level, unsigned char *smem) {
         const int i = w * 32 * S::ITEMS + j * 32 + lane;
         key[j] = i < tn ? ld_key<K>(src + tbase + i) : (K)0;
       }
-      // 64-bit keys: the next tile into L2 while this one is ranked (with
-      // 32-bit keys this measured slower: 16.3 -> 16.8 ms for the two
-      // scatters of 10^9 key/value pairs, against 26.0 -> 24.0 ms for 64-bit)
-      if (sizeof(K) == 8 && threadIdx.x == 0) {
-        prefetch_l2<K>(src, tbase + S::TILE, S::TILE, P.n);
-        if constexpr (HV) prefetch_l2<K>(vsrc, tbase, 2 * S::TILE, P.n);  // this and the next
+      // L2 prefetches, by measurement (10^9 records, the two scatters): 64-bit
+      // keys fetch the next tile's keys and this and the next tile's values
+      // (key/value 26.0 -> 24.0 ms); 32-bit key/value pairs fetch this tile's
+      // values, which are read only after the ranking (15.5 -> 14.7 ms; the
+      // next tile's keys as well measured 14.9 ms); 32-bit keys alone fetch
+      // the next tile's keys (9.8 -> 9.0 ms)
+      if (threadIdx.x == 0) {
+        if constexpr (sizeof(K) == 8) {
+          prefetch_l2<K>(src, tbase + S::TILE, S::TILE, P.n);
+          if constexpr (HV) prefetch_l2<K>(vsrc, tbase, 2 * S::TILE, P.n);
+        } else if constexpr (HV) {
+          prefetch_l2<K>(vsrc, tbase, S::TILE, P.n);
+        } else {
+          prefetch_l2<K>(src, tbase + S::TILE, S::TILE, P.n);
+        }
       }
       {
         uint4 *z = (uint4 *)slots;
