@@ -20,6 +20,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 namespace dts {
 
 constexpr int NT = 512;                       // threads per CTA, every phase

@@ -1012,6 +1012,14 @@ __host__ __device__ constexpr int fin_fb() {
   return fb;
 }
 
+// key - kb in the key's own width (32-bit arithmetic for 32-bit keys).
+template <typename K>
+using KOff = typename std::conditional<sizeof(K) == 4, uint32_t, uint64_t>::type;
+template <typename K>
+__device__ __forceinline__ KOff<K> key_off(K k, K kb) {
+  return (KOff<K>)(k - kb);
+}
+
 // Layout of the base-case area for composites of type CT: the bins (thread
 // t's run of per bins at t (per + 1)), the placed composites, the values in
 // input order.
@@ -1037,7 +1045,7 @@ __device__ __forceinline__ void fin_hist(const Rec<K, HV> (&rr)[Shape<K, HV>::FI
     const int i = j * NT + threadIdx.x;
     if (j < R && i < n) {
       if constexpr (HV) vst[i] = rr[j].v;
-      const unsigned b = (unsigned)((uint64_t)(K)(rr[j].k - kb) >> bsh);
+      const unsigned b = (unsigned)(key_off<K>(rr[j].k, kb) >> bsh);
       atomicAdd(&bins[b + (b >> psh)], 1u);
     }
   }
@@ -1073,8 +1081,8 @@ __device__ __forceinline__ bool fin_core(const Rec<K, HV> (&rr)[Shape<K, HV>::FI
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int psh = fb - 9, per = 1 << psh;
   auto comp = [&](K k, int i) -> CT {
-    if constexpr (HV) return ((CT)(K)(k - kb) << IB) | (CT)i;
-    else return (CT)(K)(k - kb);
+    if constexpr (HV) return ((CT)key_off<K>(k, kb) << IB) | (CT)i;
+    else return (CT)key_off<K>(k, kb);
   };
   // thread t owns bins [t per, (t+1) per): bin starts = exclusive prefix
   unsigned *mb = bins + threadIdx.x * (per + 1);
@@ -1098,8 +1106,7 @@ __device__ __forceinline__ bool fin_core(const Rec<K, HV> (&rr)[Shape<K, HV>::FI
   if (lane == 0) atomicMax(cmax, mx);
   __syncthreads();
   if (*cmax > (unsigned)S::FIN_CMAX) return false;
-  unsigned run = x - sum;
-  for (int q = 0; q < w; ++q) run += wsum[q];
+  unsigned run = x - sum + __reduce_add_sync(0xffffffffu, lane < w ? wsum[lane] : 0u);
   const unsigned my0 = run;
 #pragma unroll
   for (int q = 0; q < PERM; ++q) {
@@ -1112,7 +1119,7 @@ __device__ __forceinline__ bool fin_core(const Rec<K, HV> (&rr)[Shape<K, HV>::FI
   for (int j = 0; j < S::FIN_IT; ++j) {
     const int i = j * NT + threadIdx.x;
     if (j < R && i < n) {
-      const unsigned b = (unsigned)((uint64_t)(K)(rr[j].k - kb) >> bsh);
+      const unsigned b = (unsigned)(key_off<K>(rr[j].k, kb) >> bsh);
       const unsigned p = atomicAdd(&bins[b + (b >> psh)], 1u);
       if (p < (unsigned)n) pc[p] = comp(rr[j].k, i);
       else bad = 1u + p;
@@ -1293,8 +1300,8 @@ __device__ void phase_finish(const Params &P, int level, unsigned char *smem) {
       for (int j = 0; j < S::FIN_IT; ++j) {
         const int i = j * NT + threadIdx.x;
         if (j < R && i < n) {
-          const uint64_t dk = (uint64_t)(K)(rr[j].k - kb0);
-          if (hi < 64 && (dk >> hi) != 0) {
+          const KOff<K> dk = key_off<K>(rr[j].k, kb0);
+          if (hi < 8 * (int)sizeof(K) && (dk >> hi) != 0) {
             bad = 1u + (unsigned)i;  // a key outside the task's range
           } else {
             if constexpr (HV) vst0[i] = rr[j].v;
