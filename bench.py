@@ -68,6 +68,8 @@ def parse():
                          "learned-always: model zones regardless")
     ap.add_argument("--autotune", action="store_true",
                     help="run the autotuner on the workload first and use its choice")
+    ap.add_argument("--heavy", default="on", choices=["on", "off"],
+                    help="off: no heavy-key detection (the paper's 'Plain' ablation)")
     return ap.parse_args()
 
 
@@ -296,8 +298,9 @@ def run_ours(args):
           "u64kv": dts.DTSORT_OP_U64_KV, "u64": dts.DTSORT_OP_U64}[args.op]
     h = dts.dtsort_create(local)
     if (args.launch_mode or args.bucketing != "digit" or args.block_tiles or args.gamma_max or
-            args.capacity):
+            args.capacity or args.heavy == "off"):
         o = dts.dtsort_get_options(h)
+        o.heavy_detection = -1 if args.heavy == "off" else 0
         o.launch_mode = args.launch_mode
         o.block_tiles = args.block_tiles
         o.gamma_max = args.gamma_max
@@ -388,6 +391,7 @@ def run_ours(args):
     if rank != 0:
         return 0
     peak, peak_kind = peaks()
+    rec_bytes = kbytes * (2 if has_v else 1)
     b_alg = B_ALG[args.op] * n
     achieved = b_alg / (ms_step / 1e3) / 1e9
     line = {
@@ -395,11 +399,16 @@ def run_ours(args):
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": args.op, "data": "synthetic",
-        "config": {"workload": "stable sort, %s, n=%d, keys %s seed %d, values = index%s"
+        "config": {"workload": "stable sort, %s, n=%d, keys %s seed %d, values = index%s%s"
                                % (args.op, n, args.dist, args.seed,
                                   "" if args.bucketing == "digit"
-                                  else ", bucketing " + args.bucketing),
-                   "n": n, "dist": args.dist, "l2": "inputs 8+ GB per step >> L2",
+                                  else ", bucketing " + args.bucketing,
+                                  ", heavy-key detection off" if args.heavy == "off" else ""),
+                   "n": n, "dist": args.dist,
+                   "l2": ("inputs %.1f GB per step >> L2 (129 MB)" % (rec_bytes * n / 1e9)
+                          if rec_bytes * n > 4 * 129e6 else
+                          "inputs %.0f MB per step: not much larger than L2 (129 MB)"
+                          % (rec_bytes * n / 1e6)),
                    "parallelism": "replicas" if world > 1 else "single"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak,

@@ -113,7 +113,7 @@ Layout make_layout(int kb, int vb, int64_t n, int64_t nsegs, const Opts &o,
   L.bmax = 12 * nt + L.maxseg + 1024;
   L.hmax = 4 * nt + L.maxseg + 1024;
   L.zmax = 8 * nt + 2 * L.maxseg + 1024;
-  L.hashmax = 8 * nt + L.maxseg + 1024;
+  L.hashmax = 16 * nt + 2 * L.maxseg + 1024;  // 2^(gamma+1) slots per subproblem
   // count matrix: one row of <= NB_HW words per block of every subproblem;
   // look-back status: one row per chunk of ks.ch rows
   const int64_t blk = (int64_t)o.blk_tiles * ks.tile;

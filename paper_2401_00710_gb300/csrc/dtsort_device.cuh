@@ -33,7 +33,7 @@ constexpr int NB_PAD = 648;                   // NB_HW + dummy bucket, padded
 constexpr int NB_PAIR = NB_PAD / 2;           // 16-bit warp counters, two per word
 constexpr int LRN_TAB_N = 512;                // learned prediction table cells
 constexpr int SMAX = 8192;                    // largest on-chip sample
-constexpr int HASH_HW = 1 << GAMMA_HW;        // hash slots for <= 256 heavy keys
+constexpr int HASH_HW = 1 << GAMMA_HW;        // hash slots: 4 per heavy key (<= 128)
 constexpr int MAXLEV = 136;                   // > 2 * 64 + slack
 constexpr int64_t COPY_CHUNK = 1 << 16;       // records per plain-copy task
 constexpr int MERGE_CHUNK = 8192;             // output records per merge item
@@ -571,8 +571,9 @@ __device__ __forceinline__ unsigned bucket_of(const BucketCtx &X, const int32_t 
     uint32_t s = hash_slot<K>(key, X.hbits);
     while (true) {
       const uint16_t id = hid[s];
+      const K k = hk[s];  // both loads of a probe issued together
       if (id == HEMPTY) break;
-      if (hk[s] == key) return id;
+      if (k == key) return id;
       s = (s + 1) & cap1;
     }
   }

@@ -65,7 +65,7 @@ NoallocLayout noalloc_layout(int64_t n) {
   L.bmax = 12 * nt + L.maxseg + 1024;
   L.hmax = 4 * nt + L.maxseg + 1024;
   L.zmax = 8 * nt + 2 * L.maxseg + 1024;
-  L.hashmax = 8 * nt + L.maxseg + 1024;
+  L.hashmax = 16 * nt + 2 * L.maxseg + 1024;  // 2^(gamma+1) slots per subproblem
   L.cwords = (int64_t)dts::NB_HW * (n / Sh::BLK + 1) + L.bmax;
   L.swords = (int64_t)dts::NB_HW * (n / ((int64_t)Sh::BLK * Sh::CH) + 1) + L.bmax;
   L.tmax = 2 * L.bmax + 2 * (n / dts::COPY_CHUNK + 1) + 1 + 4096;

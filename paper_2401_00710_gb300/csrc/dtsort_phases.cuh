@@ -230,7 +230,7 @@ __device__ void phase_setup(const Params &P, int level, unsigned char *smem) {
       hm = (1 << (g - 1)) < HEAVY_HW ? (1 << (g - 1)) : HEAVY_HW;
       nbm = (1 << g) + hm + 1;
       zm = (1 << g) + 1;
-      hsm = 1 << g;
+      hsm = (1 << (g + 1)) < HASH_HW ? (1 << (g + 1)) : HASH_HW;  // load <= 1/4
       cm = nblk * nbm;
       stm = nchk * nbm;
     }
@@ -418,7 +418,7 @@ __device__ void phase_sample(const Params &P, int level, unsigned char *smem) {
     int hbits = 0;
     if (nh > 0) {
       hbits = 1;
-      while ((1 << hbits) < 2 * nh) ++hbits;
+      while ((1 << hbits) < 4 * nh) ++hbits;  // load factor <= 1/4: light keys stop early
       const int cap = 1 << hbits;
       for (int i = threadIdx.x; i < cap; i += NT) hid[i] = HEMPTY;
       __syncthreads();
@@ -1020,6 +1020,18 @@ __device__ __forceinline__ KOff<K> key_off(K k, K kb) {
   return (KOff<K>)(k - kb);
 }
 
+// Bin of a record: the top fb bits of its composite (key - kb) << IB | i,
+// whose key part has `bits` bits: ksh = max(bits - fb, 0) key bits are
+// dropped, and when the key part is narrower than fb the top ish =
+// max(fb - bits, 0) index bits fill in (so that the records of one key value
+// spread over bins by position; without values there are no index bits and
+// ish is 0).
+template <typename K, bool HV>
+__device__ __forceinline__ unsigned fin_bin(KOff<K> dk, int i, int ksh, int ish) {
+  if constexpr (HV) return ((unsigned)(dk >> ksh) << ish) | ((unsigned)i >> (FIN_IB - ish));
+  else return (unsigned)(dk >> ksh);
+}
+
 // Layout of the base-case area for composites of type CT: the bins (thread
 // t's run of per bins at t (per + 1)), the placed composites, the values in
 // input order.
@@ -1031,11 +1043,12 @@ struct FinArea {
 };
 
 // Histogram of a task's records (item j of thread t is record i = j NT + t,
-// keys in [kb, kb + 2^bits)) on bins = (key - kb) >> bsh, and the values in
-// input order; the bins must be zero.
+// keys in [kb, kb + 2^bits)) on bins fin_bin(key - kb, i, ksh, ish), and the
+// values in input order; the bins must be zero.
 template <typename K, bool HV, typename CT>
 __device__ __forceinline__ void fin_hist(const Rec<K, HV> (&rr)[Shape<K, HV>::FIN_IT], int n,
-                                         int R, K kb, int bsh, int psh, unsigned char *region) {
+                                         int R, K kb, int ksh, int ish, int psh,
+                                         unsigned char *region) {
   using S = Shape<K, HV>;
   using A = FinArea<K, HV, CT>;
   unsigned *bins = (unsigned *)region;
@@ -1045,7 +1058,7 @@ __device__ __forceinline__ void fin_hist(const Rec<K, HV> (&rr)[Shape<K, HV>::FI
     const int i = j * NT + threadIdx.x;
     if (j < R && i < n) {
       if constexpr (HV) vst[i] = rr[j].v;
-      const unsigned b = (unsigned)(key_off<K>(rr[j].k, kb) >> bsh);
+      const unsigned b = fin_bin<K, HV>(key_off<K>(rr[j].k, kb), i, ksh, ish);
       atomicAdd(&bins[b + (b >> psh)], 1u);
     }
   }
@@ -1053,7 +1066,7 @@ __device__ __forceinline__ void fin_hist(const Rec<K, HV> (&rr)[Shape<K, HV>::FI
 
 // One-pass base case of a task of n <= FIN_CAP records held in registers
 // (item j of thread t is record i = j NT + t), keys in [kb, kb + 2^bits),
-// after fin_hist has counted its 2^fb bins (bin = (key - kb) >> bsh).  Each
+// after fin_hist has counted its 2^fb bins (fin_bin with ksh, ish).  Each
 // record is the composite c = (key - kb) << FIN_IB | i (without values
 // c = key - kb): with values the composites are distinct and their order is
 // the order of (key, original index), i.e. the stable order.  The bins'
@@ -1067,7 +1080,8 @@ __device__ __forceinline__ void fin_hist(const Rec<K, HV> (&rr)[Shape<K, HV>::FI
 // it returns false).
 template <typename K, bool HV, typename CT>
 __device__ __forceinline__ bool fin_core(const Rec<K, HV> (&rr)[Shape<K, HV>::FIN_IT], int n,
-                                         int R, K kb, int fb, int bsh, unsigned char *region,
+                                         int R, K kb, int fb, int ksh, int ish,
+                                         unsigned char *region,
                                          unsigned *wsum, unsigned *cmax, K *kd, K *vd,
                                          unsigned &bad) {
   using S = Shape<K, HV>;
@@ -1105,7 +1119,10 @@ __device__ __forceinline__ bool fin_core(const Rec<K, HV> (&rr)[Shape<K, HV>::FI
   if (lane == 31) wsum[w] = x;
   if (lane == 0) atomicMax(cmax, mx);
   __syncthreads();
-  if (*cmax > (unsigned)S::FIN_CMAX) return false;
+  // without values, bins that hold one key value each need no sorting
+  const bool presorted = !HV && ksh == 0;
+  if (presorted) multi = 0;
+  if (!presorted && *cmax > (unsigned)S::FIN_CMAX) return false;
   unsigned run = x - sum + __reduce_add_sync(0xffffffffu, lane < w ? wsum[lane] : 0u);
   const unsigned my0 = run;
 #pragma unroll
@@ -1119,7 +1136,7 @@ __device__ __forceinline__ bool fin_core(const Rec<K, HV> (&rr)[Shape<K, HV>::FI
   for (int j = 0; j < S::FIN_IT; ++j) {
     const int i = j * NT + threadIdx.x;
     if (j < R && i < n) {
-      const unsigned b = (unsigned)(key_off<K>(rr[j].k, kb) >> bsh);
+      const unsigned b = fin_bin<K, HV>(key_off<K>(rr[j].k, kb), i, ksh, ish);
       const unsigned p = atomicAdd(&bins[b + (b >> psh)], 1u);
       if (p < (unsigned)n) pc[p] = comp(rr[j].k, i);
       else bad = 1u + p;
@@ -1278,7 +1295,8 @@ __device__ void phase_finish(const Params &P, int level, unsigned char *smem) {
     const int hi = tk.hi;
     const int ct = hi + IB <= 32 ? 1 : (WIDE && hi + IB <= 64 ? 2 : 0);
     const int fb0 = min(max(bitlen64((uint64_t)(n - 1)) + 1, 9), ct == 2 ? FBM64 : FBM32);
-    const int bsh0 = hi > fb0 ? hi - fb0 : 0;
+    const int ksh0 = hi > fb0 ? hi - fb0 : 0;
+    const int ish0 = HV && fb0 > hi ? fb0 - hi : 0;
     const int psh0 = fb0 - 9;
     const K kb0 = (K)tk.base;
     unsigned *bins = (unsigned *)region;
@@ -1305,7 +1323,7 @@ __device__ void phase_finish(const Params &P, int level, unsigned char *smem) {
             bad = 1u + (unsigned)i;  // a key outside the task's range
           } else {
             if constexpr (HV) vst0[i] = rr[j].v;
-            const unsigned b = (unsigned)(dk >> bsh0);
+            const unsigned b = fin_bin<K, HV>(dk, i, ksh0, ish0);
             atomicAdd(&bins[b + (b >> psh0)], 1u);
           }
         }
@@ -1319,11 +1337,11 @@ __device__ void phase_finish(const Params &P, int level, unsigned char *smem) {
     bool done = false;
     bool wide = false;  // 64-bit composites: they overlap the widest bin layout
     if (ct == 1) {
-      done = fin_core<K, HV, uint32_t>(rr, n, R, kb0, fb0, bsh0, region, wsum, &cmax_sh[par], kd,
-                                       vd, bad);
+      done = fin_core<K, HV, uint32_t>(rr, n, R, kb0, fb0, ksh0, ish0, region, wsum,
+                                       &cmax_sh[par], kd, vd, bad);
     } else if (ct == 2) {
       if constexpr (WIDE)
-        done = wide = fin_core<K, HV, uint64_t>(rr, n, R, kb0, fb0, bsh0, region, wsum,
+        done = wide = fin_core<K, HV, uint64_t>(rr, n, R, kb0, fb0, ksh0, ish0, region, wsum,
                                                 &cmax_sh[par], kd, vd, bad);
     }
     if (!done) {
@@ -1368,18 +1386,19 @@ __device__ void phase_finish(const Params &P, int level, unsigned char *smem) {
         const int bl = bitlen64(span);
         const int ct1 = bl + IB <= 32 ? 1 : (WIDE && bl + IB <= 64 ? 2 : 0);
         const int fb1 = min(max(bitlen64((uint64_t)(n - 1)) + 1, 9), ct1 == 2 ? FBM64 : FBM32);
-        const int bsh1 = bl > fb1 ? bl - fb1 : 0;
+        const int ksh1 = bl > fb1 ? bl - fb1 : 0;
+        const int ish1 = HV && fb1 > bl ? fb1 - bl : 0;
         if (ct1 == 1) {
-          fin_hist<K, HV, uint32_t>(rr, n, R, kmin, bsh1, fb1 - 9, region);
+          fin_hist<K, HV, uint32_t>(rr, n, R, kmin, ksh1, ish1, fb1 - 9, region);
           __syncthreads();
-          done = fin_core<K, HV, uint32_t>(rr, n, R, kmin, fb1, bsh1, region, wsum, &cmax_sh[2],
-                                           kd, vd, bad);
+          done = fin_core<K, HV, uint32_t>(rr, n, R, kmin, fb1, ksh1, ish1, region, wsum,
+                                           &cmax_sh[2], kd, vd, bad);
         } else if (ct1 == 2) {
           if constexpr (WIDE) {
-            fin_hist<K, HV, uint64_t>(rr, n, R, kmin, bsh1, fb1 - 9, region);
+            fin_hist<K, HV, uint64_t>(rr, n, R, kmin, ksh1, ish1, fb1 - 9, region);
             __syncthreads();
-            done = wide = fin_core<K, HV, uint64_t>(rr, n, R, kmin, fb1, bsh1, region, wsum,
-                                                    &cmax_sh[2], kd, vd, bad);
+            done = wide = fin_core<K, HV, uint64_t>(rr, n, R, kmin, fb1, ksh1, ish1, region,
+                                                    wsum, &cmax_sh[2], kd, vd, bad);
           }
         }
       }
