@@ -106,14 +106,14 @@ typedef struct {
   int32_t debug_fault;       /* testing only: 1 = the second look-back chunk of
                                 the first distribution never publishes its
                                 status, so its successors' waits expire */
-  int32_t launch_mode;       /* 0 (default): for a single array, the levels a
-                                uniformly distributed input of this size needs
-                                run as one launch per phase, queued without
-                                host synchronisation (each phase checks on the
-                                device whether it has work), then one
+  int32_t launch_mode;       /* 0 (default): the levels a uniformly
+                                distributed input of n keys needs (n = the
+                                total for a segmented call, which bounds every
+                                array) run as one launch per phase, queued
+                                without host synchronisation (each phase checks
+                                on the device whether it has work), then one
                                 persistent cooperative launch takes any further
-                                levels and the merges; a segmented call is the
-                                persistent launch alone.  No host
+                                levels and the merges.  No host
                                 synchronisation; capturable in a CUDA graph.
                                 1: one launch per phase with the level loop on
                                 the host (a profiling aid: every phase appears

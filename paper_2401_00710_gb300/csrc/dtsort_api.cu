@@ -469,10 +469,11 @@ dtsort_status run_sort(dtsort_handle h, int op, void *keys, void *vals, const in
     h->launches += cnt;
     return from_cuda(e);
   }
-  // single arrays: the levels a uniform input needs run as separate phase
-  // launches, the rest (if any) in the persistent kernel
-  const int head = (h->opt.launch_mode == 0 && !offsets)
-                       ? predict_levels(n, 8 * kb, o, L.target) : 0;
+  // the levels a uniform input of n keys needs run as separate phase
+  // launches, the rest (if any) in the persistent kernel; for a segmented
+  // call n (the total) bounds every array's size, and a queued level without
+  // work returns at once on the device
+  const int head = h->opt.launch_mode == 0 ? predict_levels(n, 8 * kb, o, L.target) : 0;
   switch (op) {
     case DTSORT_OP_U32: e = dts::launch_u32(P, grid, head, *ks, h->nsm, s); break;
     case DTSORT_OP_U32_KV: e = dts::launch_u32kv(P, grid, head, *ks, h->nsm, s); break;
