@@ -88,6 +88,7 @@ struct Task {
   int32_t hi;
   uint8_t src, dst, kind, pad;
 };
+static_assert(sizeof(Task) == 32, "a task descriptor is two 16-byte copies");
 
 // An MSD zone with heavy buckets, merged after its light bucket is sorted.
 struct MZone {
@@ -439,6 +440,16 @@ __device__ __forceinline__ unsigned warp_rank(unsigned b, unsigned *slot, unsign
     __syncwarp();
   }
   return old + __popc(peers & lanemask_lt());
+}
+
+// 16 bytes global -> shared without registers (cp.async, L2 only); both
+// addresses 16-byte aligned.  cp_async_wait_all() waits for this thread's.
+__device__ __forceinline__ void cp_async16(void *sdst, const void *gsrc) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_all;" ::: "memory");
 }
 
 // Asks L2 to fetch elements [first, first + count) of array a (clipped to

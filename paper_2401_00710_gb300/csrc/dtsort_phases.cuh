@@ -82,7 +82,7 @@ constexpr size_t smem_bytes() {
   fin += 16 + (size_t)S::FIN_BYTES;
   fin += 16 + 2 * (size_t)NWARP * FIN_NB;
   fin += 16 + 4 * FIN_NB * 2;
-  fin += 16 + 4 * (NWARP + 1) + 16 + 4 * NWARP + 4 * 16 + 16 + 256;
+  fin += 16 + 4 * (NWARP + 1) + 16 + 4 * NWARP + 4 * 16 + 16 + 16 + 2 * sizeof(Task) + 256;
   // sampler
   size_t smp = 16 + sizeof(K) * SMAX + 16 + sizeof(K) * (SMAX / 2 + 8) + 16 + 4 * 1024 +
                16 + sizeof(K) * HASH_HW + 16 + 2 * HASH_HW + 512;
@@ -1153,16 +1153,34 @@ __device__ __forceinline__ bool fin_core(const Rec<K, HV> (&rr)[Shape<K, HV>::FI
       bad = 1u + e;
       continue;
     }
-    for (unsigned a = s + 1; a < e; ++a) {
-      const CT v = pc[a];
-      unsigned b = a;
-      while (b > s) {
-        const CT u = pc[b - 1];
-        if (u <= v) break;
-        pc[b] = u;
-        --b;
+    const unsigned m = e - s;
+    if (m == 2) {  // most multi-record bins: loads together, one exchange
+      const CT v0 = pc[s], v1 = pc[s + 1];
+      if (v1 < v0) {
+        pc[s] = v1;
+        pc[s + 1] = v0;
       }
-      pc[b] = v;
+    } else if (m == 3) {  // a three-exchange network
+      CT v0 = pc[s], v1 = pc[s + 1], v2 = pc[s + 2];
+      CT t;
+      if (v1 < v0) { t = v0; v0 = v1; v1 = t; }
+      if (v2 < v1) { t = v1; v1 = v2; v2 = t; }
+      if (v1 < v0) { t = v0; v0 = v1; v1 = t; }
+      pc[s] = v0;
+      pc[s + 1] = v1;
+      pc[s + 2] = v2;
+    } else {
+      for (unsigned a = s + 1; a < e; ++a) {
+        const CT v = pc[a];
+        unsigned b = a;
+        while (b > s) {
+          const CT u = pc[b - 1];
+          if (u <= v) break;
+          pc[b] = u;
+          --b;
+        }
+        pc[b] = v;
+      }
     }
   }
   __syncthreads();
@@ -1192,6 +1210,7 @@ __device__ void phase_finish(const Params &P, int level, unsigned char *smem) {
   // per-task scalars, two copies: task k uses copy k & 1 while thread 0
   // prepares the other for task k + 1; cmax_sh[2]: the min/max path's own
   long long *task_sh = cv.take<long long>(2);
+  Task *tdesc = cv.take<Task>(2);
   K *kmin_sh = cv.take<K>(2);
   K *kmax_sh = cv.take<K>(2);
   unsigned *cmax_sh = cv.take<unsigned>(3);
@@ -1209,16 +1228,25 @@ __device__ void phase_finish(const Params &P, int level, unsigned char *smem) {
   unsigned bad = 0;  // self-check: a base-case slot out of range, reported once
   // every bin of the widest layout starts at zero for every task (cleared
   // again at the end of each task that used them)
-  auto zero_bins = [&]() {
+  constexpr int ZFULL = (1 << FBM32) + NT;  // words of the widest bin layout
+  auto zero_bins = [&](int words) {
     uint4 *z = (uint4 *)region;
-    for (int i = threadIdx.x; i < ((1 << FBM32) + NT) / 4; i += NT) z[i] = make_uint4(0, 0, 0, 0);
+    for (int i = threadIdx.x; i < (words + 3) / 4; i += NT) z[i] = make_uint4(0, 0, 0, 0);
   };
   // Tasks are claimed two ahead by thread 0: q1 = the next task (its id known,
   // its records prefetched into L2 during this one), q2 = the one after (its
   // claim in flight until the end of this task).
+  // The descriptors of the current task and the next one are copied into
+  // shared memory by thread 0 (asynchronously, no registers), so a task
+  // starts without a global load.
   long long q1 = 0, q2 = 0;
-  long long dn_start = 0, dn_size = 0;  // thread 0: the next task's range
-  unsigned dn_src = 2;                  // and source buffer (2: none)
+  auto fetch_desc = [&](int q, long long t) {
+    if (t < ntasks) {
+      const char *g = (const char *)&P.tasks[t];
+      cp_async16(&tdesc[q], g);
+      cp_async16((char *)&tdesc[q] + 16, g + 16);
+    }
+  };
   auto reset = [&](int q) {
     kmin_sh[q] = (K)~(K)0;
     kmax_sh[q] = (K)0;
@@ -1228,20 +1256,25 @@ __device__ void phase_finish(const Params &P, int level, unsigned char *smem) {
   auto advance = [&](int q) {
     task_sh[q] = q1;
     reset(q);
+    cp_async_wait_all();  // the next task's descriptor has landed
   };
-  auto prefetch_next = [&]() {
-    if (q1 < ntasks && dn_src <= 1u && dn_start >= 0 && dn_size > 0) {
-      const int64_t m = dn_size < S::FIN_CAP ? dn_size : S::FIN_CAP;
-      prefetch_l2<K>((const K *)P.keys[dn_src], dn_start, m, P.n);
-      if constexpr (HV) prefetch_l2<K>((const K *)P.vals[dn_src], dn_start, m, P.n);
+  auto prefetch_next = [&](int q) {
+    const Task &d = tdesc[q];
+    if (q1 < ntasks && d.src <= 1 && d.start >= 0 && d.size > 0) {
+      const int64_t m = d.size < S::FIN_CAP ? d.size : S::FIN_CAP;
+      prefetch_l2<K>((const K *)P.keys[d.src], d.start, m, P.n);
+      if constexpr (HV) prefetch_l2<K>((const K *)P.vals[d.src], d.start, m, P.n);
     }
   };
   int par = 0;
-  zero_bins();
+  zero_bins(ZFULL);
   if (threadIdx.x == 0) {
-    task_sh[0] = atomic_add_ll(&c->task_ctr, 1ll);
+    const long long t0 = atomic_add_ll(&c->task_ctr, 1ll);
+    task_sh[0] = t0;
     q1 = atomic_add_ll(&c->task_ctr, 1ll);
     reset(0);
+    fetch_desc(0, t0);
+    cp_async_wait_all();
   }
   __syncthreads();
   while (true) {
@@ -1249,14 +1282,9 @@ __device__ void phase_finish(const Params &P, int level, unsigned char *smem) {
     if (ti >= ntasks) break;
     if (threadIdx.x == 0) {
       q2 = atomic_add_ll(&c->task_ctr, 1ll);
-      if (q1 < ntasks) {
-        const Task *d = &P.tasks[q1];
-        dn_start = ld_cg64((const long long *)&d->start);
-        dn_size = ld_cg64((const long long *)&d->size);
-        dn_src = (unsigned)__ldcg((const unsigned char *)&d->src);
-      }
+      fetch_desc(par ^ 1, q1);
     }
-    const Task tk = ldcg_obj(&P.tasks[ti]);
+    const Task tk = tdesc[par];
     const bool ok = !(tk.src > 1 || tk.dst > 1 || tk.start < 0 || tk.size < 0 ||
                       tk.start + tk.size > P.n ||
                       (tk.kind != TASK_COPY && (tk.size > S::FIN_CAP || tk.hi < 0 || tk.hi > 64)));
@@ -1332,10 +1360,12 @@ __device__ void phase_finish(const Params &P, int level, unsigned char *smem) {
     __syncthreads();
     if (threadIdx.x == 0) {
       advance(par ^ 1);
-      prefetch_next();
+      prefetch_next(par ^ 1);
     }
     bool done = false;
     bool wide = false;  // 64-bit composites: they overlap the widest bin layout
+    // words of the bin area this task may leave nonzero (cleared at its end)
+    int dirty = ct ? (1 << fb0) + NT : 0;
     if (ct == 1) {
       done = fin_core<K, HV, uint32_t>(rr, n, R, kb0, fb0, ksh0, ish0, region, wsum,
                                        &cmax_sh[par], kd, vd, bad);
@@ -1368,7 +1398,8 @@ __device__ void phase_finish(const Params &P, int level, unsigned char *smem) {
         }
       }
       if (threadIdx.x == 0) cmax_sh[2] = 0u;
-      zero_bins();
+      zero_bins(ZFULL);
+      dirty = ZFULL;
       __syncthreads();
       const K kmin = kmin_sh[par];
       const uint64_t span = (uint64_t)kmax_sh[par] - (uint64_t)kmin;
@@ -1407,6 +1438,7 @@ __device__ void phase_finish(const Params &P, int level, unsigned char *smem) {
       // a bin with many equal-prefix keys: stable LSD passes over the task's
       // hi bits
       my_lsd += 1;
+      dirty = ZFULL;
 #pragma unroll
       for (int j = 0; j < S::FIN_IT; ++j) {
         const int i = j * NT + threadIdx.x;
@@ -1493,7 +1525,7 @@ __device__ void phase_finish(const Params &P, int level, unsigned char *smem) {
     // clear the bins for the next task once no thread reads this task's
     // composites where they overlap them
     if (wide) __syncthreads();
-    zero_bins();
+    zero_bins(wide ? ZFULL : dirty);
     __syncthreads();
     if (threadIdx.x == 0) q1 = q2;
     par ^= 1;
