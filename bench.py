@@ -215,7 +215,10 @@ def cpu_oracle_time(args, sample):
     import oracle
     kd = key_dtype(args.op)
     keys = sample_keys(args, sample)
-    vals = gen.iota(sample, kd) if args.op.endswith("kv") else None
+    vals = None
+    if args.op.endswith("kv"):
+        vals = (gen.edge_src(sample, kd, E=args.n) if args.dist == "edges"
+                else gen.iota(sample, kd))
     cores = oracle.default_threads()
     t0 = time.perf_counter()
     oracle.stable_sort(keys, vals, nthreads=cores)
@@ -289,7 +292,10 @@ def run_ours(args):
     hv = None
     if has_v:
         hv = torch.empty(n, dtype=tdt, pin_memory=True)
-        gen.fill_iota(hv.data_ptr(), n, kbytes)
+        if args.dist == "edges":  # graph transpose: values = the edges' sources
+            gen.fill_edge_src(hv.data_ptr(), n, kbytes)
+        else:
+            gen.fill_iota(hv.data_ptr(), n, kbytes)
     pk = hk.to(dev)
     pv = hv.to(dev) if has_v else None
     k = torch.empty_like(pk)
@@ -399,8 +405,11 @@ def run_ours(args):
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": args.op, "data": "synthetic",
-        "config": {"workload": "stable sort, %s, n=%d, keys %s seed %d, values = index%s%s"
+        "config": {"workload": "stable sort, %s, n=%d, keys %s seed %d, values = %s%s%s"
                                % (args.op, n, args.dist, args.seed,
+                                  "the edges' sources (graph transpose of a power-law "
+                                  "edge list over 2^26 vertices)" if args.dist == "edges"
+                                  else "index",
                                   "" if args.bucketing == "digit"
                                   else ", bucketing " + args.bucketing,
                                   ", heavy-key detection off" if args.heavy == "off" else ""),

@@ -17,7 +17,8 @@ _SO = os.path.join(_HERE, "_build", "libgen.so")
 _lib = None
 
 UNIFORM, ZIPF, ZIPF_HASHED, EXP, BITEXP, DISTINCT, HEAVYMIX, SKEWMIX, \
-    BEXP_PAPER, UNIF_MU = range(10)
+    BEXP_PAPER, UNIF_MU, EDGES = range(11)
+EDGE_VERTICES = 1 << 26  # power-law edge lists: 2^26 vertices
 
 
 def build(force=False):
@@ -49,6 +50,9 @@ def lib():
                                         ctypes.c_double, ctypes.c_double,
                                         ctypes.c_void_p, ctypes.c_void_p]
         L.gen_segment_sizes.restype = ctypes.c_int
+        L.gen_edge_src.argtypes = [ctypes.c_int, ctypes.c_int64, ctypes.c_int64,
+                                   ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p]
+        L.gen_edge_src.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -81,6 +85,20 @@ def fill_iota(out_ptr, n, vbytes, first=0):
     lib().gen_iota(vbytes, first, n, out_ptr)
 
 
+def fill_edge_src(out_ptr, n, vbytes, E=None, V=EDGE_VERTICES, first=0):
+    """Sources of edges [first, first+n) of a list of E (default n) edges over
+    V vertices ordered by source: src_i = floor(i V / E)."""
+    if lib().gen_edge_src(vbytes, first, n, n if E is None else E, V, out_ptr):
+        raise ValueError("bad edge-list request")
+
+
+def edge_src(n, dtype=np.uint32, E=None, V=EDGE_VERTICES, first=0):
+    dtype = np.dtype(dtype)
+    out = np.empty(n, dtype=dtype)
+    fill_edge_src(out.ctypes.data, n, dtype.itemsize, E, V, first)
+    return out
+
+
 def rng(seed, stream, i):
     return lib().gen_rng(seed, stream, i)
 
@@ -107,6 +125,9 @@ U32_FAMILIES = {
     "distinct10": (DISTINCT, np.uint32, 10, 0.0),
     "bexp30": (BEXP_PAPER, np.uint32, 30, 0.0),
     "unif1e3": (UNIF_MU, np.uint32, 1e3, 0.0),
+    # graph transpose: destinations of a power-law edge list (in-degree
+    # Zipf 1.0 over 2^26 vertices); the values are the edges' sources
+    "edges": (EDGES, np.uint32, 1.0, float(EDGE_VERTICES)),
 }
 U64_FAMILIES = {
     "uniform": (UNIFORM, np.uint64, 0.0, 0.0),

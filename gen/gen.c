@@ -22,6 +22,10 @@
  *                    clamped to [0, 2^63-1]
  *   GEN_BEXP_PAPER   every bit is 0 with probability 1/t (paper's BExp-t)
  *   GEN_UNIF_MU      mu distinct keys: key = mix(rng mod mu)
+ *   GEN_EDGES        destination vertex of edge i of a power-law edge list:
+ *                    Zipf(s) rank over V vertices (V a power of two), the
+ *                    ranks scattered over [0, V) by an odd multiplier mod V;
+ *                    the matching sources come from gen_edge_src
  */
 #include <math.h>
 #include <pthread.h>
@@ -41,6 +45,7 @@ enum {
   GEN_SKEWMIX = 7,
   GEN_BEXP_PAPER = 8,
   GEN_UNIF_MU = 9,
+  GEN_EDGES = 10,
 };
 
 #define G_GOLDEN 0x9E3779B97F4A7C15ULL
@@ -188,6 +193,10 @@ static uint64_t draw_one(const gen_job_t *j, uint64_t i) {
       uint64_t r = gen_rng(seed, 0, i) % (uint64_t)j->p1;
       return w == 32 ? (uint64_t)g_fmix32((uint32_t)r) : g_fmix(r + 1);
     }
+    case GEN_EDGES: {
+      uint64_t rk = zipf_draw(&j->zipf, seed, 0, i) - 1;
+      return (rk * G_GOLDEN) & ((uint64_t)j->p2 - 1);
+    }
     default:
       return 0;
   }
@@ -228,7 +237,9 @@ int gen_keys(int kind, int kbytes, double p1, double p2, uint64_t seed,
   proto.p1 = p1;
   proto.p2 = p2;
   proto.seed = seed;
-  if (kind == GEN_ZIPF || kind == GEN_ZIPF_HASHED) zipf_init(&proto.zipf, p1, p2);
+  if (kind == GEN_ZIPF || kind == GEN_ZIPF_HASHED || kind == GEN_EDGES)
+    zipf_init(&proto.zipf, p1, p2);
+  if (kind == GEN_EDGES && (p2 < 2.0 || (((uint64_t)p2) & ((uint64_t)p2 - 1)) != 0)) return -1;
   if (kind == GEN_SKEWMIX) zipf_init(&proto.zipf, 1.2, 1e9);
   if (kind == GEN_DISTINCT || kind == GEN_HEAVYMIX) {
     int64_t k = kind == GEN_DISTINCT ? (int64_t)p1 : (int64_t)p2;
@@ -271,6 +282,20 @@ int gen_iota(int vbytes, int64_t first, int64_t n, void *out) {
   } else {
     uint64_t *o = (uint64_t *)out;
     for (int64_t i = 0; i < n; ++i) o[i] = (uint64_t)(first + i);
+  }
+  return 0;
+}
+
+/* Source vertices of edges [first, first+n) of a list of E edges over V
+ * vertices ordered by source: src_i = floor(i V / E), every vertex about E/V
+ * out-edges. */
+int gen_edge_src(int vbytes, int64_t first, int64_t n, int64_t E, int64_t V, void *out) {
+  if (E <= 0 || V <= 0 || V > 0xFFFFFFFFLL || first < 0 || first + n > E) return -1;
+  for (int64_t i = 0; i < n; ++i) {
+    const uint64_t src = (uint64_t)(((unsigned __int128)(uint64_t)(first + i) * (uint64_t)V) /
+                                    (uint64_t)E);
+    if (vbytes == 4) ((uint32_t *)out)[i] = (uint32_t)src;
+    else ((uint64_t *)out)[i] = src;
   }
   return 0;
 }

@@ -18,7 +18,10 @@ struct Shape {
   // bins, placed composites and values (see fin_onepass)
   static constexpr int FIN_BYTES = 96 * 1024;
   static constexpr int FIN_IT = FIN_CAP / NT;           // base-case items / thread
-  static constexpr int FIN_CMAX = 16;                   // largest bin sorted in place
+  // largest bin sorted in place by its owner thread: without values a big
+  // bin is mostly one key (insertion sort is linear on equal keys); with
+  // values the composites all differ (10^9 u32 KV measured: 64 is slower)
+  static constexpr int FIN_CMAX = HV ? 16 : 64;
   static constexpr int STAGE = TILE * KB;               // scatter staging (keys or values)
   static constexpr int BLK_TILES = 8;                   // tiles per count-matrix row
   static constexpr int BLK = BLK_TILES * TILE;          // records per block

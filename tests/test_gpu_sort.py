@@ -64,6 +64,15 @@ def test_u32_kv_families(G, name):
     check(G, keys, vals)
 
 
+def test_graph_transpose_edges(G):
+    # a power-law edge list ordered by source, sorted stably by destination
+    # (the transpose): each destination's sources stay in increasing order
+    n = 4_000_037
+    dst = gen.family("edges", n, np.uint32, seed=5)
+    src = gen.edge_src(n, np.uint32)
+    check(G, dst, src)
+
+
 @pytest.mark.parametrize("name", ["uniform", "zipf1.2", "distinct10", "bitexp"])
 def test_u32_key_only(G, name):
     n = 2_500_001

@@ -504,3 +504,24 @@ def test_check_stable_accepts_exactly_the_stable_sort(dtype):
     ix = io.copy()
     ix[-1] = n
     assert oracle.check_stable(keys, ko, ix) == n - 1
+
+
+def test_edge_list_generator():
+    # the graph-transpose workload: sources non-decreasing with about E/V
+    # out-edges each, destinations Zipf(1) over V vertices (the busiest one
+    # takes about 1/H_V of the edges), and the stable sort by destination
+    # keeps each destination's sources increasing
+    n = 1_000_000
+    V = gen.EDGE_VERTICES
+    dst = gen.family("edges", n, np.uint32, seed=1)
+    src = gen.edge_src(n, np.uint32)
+    assert int(dst.max()) < V
+    assert (np.diff(src.astype(np.int64)) >= 0).all()
+    assert src[0] == 0 and int(src[-1]) == (n - 1) * V // n
+    _, cnt = np.unique(dst, return_counts=True)
+    H = np.log(V) + 0.5772156649
+    assert abs(cnt.max() / n - 1.0 / H) < 0.1 / H
+    k, v = oracle.stable_sort(dst, src)
+    same = k[1:] == k[:-1]
+    assert (v[1:][same] >= v[:-1][same]).all()
+
