@@ -462,7 +462,7 @@ def segmented_passes(size, cap, gamma=9):
     import math
     if size <= cap:
         return 1
-    return 1 + max(1, math.ceil(math.log2(size / (0.7 * cap)) / gamma))
+    return 1 + max(1, math.ceil(math.log2(size / (0.85 * cap)) / gamma))
 
 
 def run_segmented(args):
@@ -581,7 +581,7 @@ def run_segmented(args):
         base = {"ms_per_step": b_ms, "value": n / (b_ms / 1e3), "unit": "keys/s",
                 "what": "one dtsort_u32_kv call per array, same GPU, same stream"}
         del sizes
-    cap = 6144
+    cap = 4608  # the base-case capacity for 32-bit keys (9 items x 512 threads)
     if rank != 0:
         dts.dtsort_destroy(h)
         return 0

@@ -105,7 +105,7 @@ Layout make_layout(int kb, int vb, int64_t n, int64_t nsegs, const Opts &o,
                    const KernelShape &ks) {
   Layout L{};
   L.cap = o.cap;
-  L.target = std::max<int64_t>(16, (int64_t)o.cap * 7 / 10);
+  L.target = std::max<int64_t>(16, (int64_t)o.cap * 85 / 100);  // bucket size the levels aim at
   const int64_t nt = n / L.target + 1;
   L.maxseg = n / (o.cap + 1) + 2;
   // per subproblem 2^gamma < 8 * size / target: buckets <= 1.5 * 2^gamma + 1,

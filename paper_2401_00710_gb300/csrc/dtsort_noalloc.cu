@@ -57,7 +57,7 @@ struct NoallocLayout {
 NoallocLayout noalloc_layout(int64_t n) {
   NoallocLayout L{};
   const int64_t cap = Sh::FIN_CAP;
-  L.target = std::max<int64_t>(16, cap * 7 / 10);
+  L.target = std::max<int64_t>(16, cap * 85 / 100);  // bucket size the levels aim at
   const int64_t nt = n / L.target + 1;
   L.maxseg = n / (cap + 1) + 2;
   // per subproblem 2^gamma < 8 * size / target: buckets <= 1.5 * 2^gamma + 1,

@@ -97,7 +97,8 @@ def test_u64_key_only(G, name):
 
 # -------------------------------------------------------------- edge cases
 EDGE_N = [1, 2, 3, 31, 32, 33, 511, 513, 3071, 3072, 3073, 4095, 4096, 4097,
-          6143, 6144, 6145, 8191, 8192, 8193, 12288, 12289, 16391, 100_003]
+          4607, 4608, 4609, 6143, 6144, 6145, 8191, 8192, 8193, 12288, 12289, 16391,
+          100_003]
 
 
 @pytest.mark.parametrize("n", EDGE_N)
