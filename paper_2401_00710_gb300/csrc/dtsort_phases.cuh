@@ -347,18 +347,18 @@ __device__ void phase_sample(const Params &P, int level, unsigned char *smem) {
       }
     }
     __syncthreads();
-    // bitonic sort of the sample on chip
+    // bitonic sort of the sample on chip: per stage every thread takes whole
+    // compare-exchange pairs (i, i + j), i the pair's lower index
     for (int kk = 2; kk <= M; kk <<= 1) {
       for (int j = kk >> 1; j > 0; j >>= 1) {
-        for (int i = threadIdx.x; i < M; i += NT) {
-          const int ixj = i ^ j;
-          if (ixj > i) {
-            const K a = Ssm[i], b = Ssm[ixj];
-            const bool up = (i & kk) == 0;
-            if ((a > b) == up) {
-              Ssm[i] = b;
-              Ssm[ixj] = a;
-            }
+        for (int pr = threadIdx.x; pr < (M >> 1); pr += NT) {
+          const int i = 2 * pr - (pr & (j - 1));
+          const int ixj = i + j;
+          const K a = Ssm[i], b = Ssm[ixj];
+          const bool up = (i & kk) == 0;
+          if ((a > b) == up) {
+            Ssm[i] = b;
+            Ssm[ixj] = a;
           }
         }
         __syncthreads();
