@@ -5,13 +5,15 @@
 //   setup    (1 CTA)   digit width per subproblem, arena reservations, tiles
 //   sample   (CTA/sub) Alg. 2 step 1: sample, sort on chip, heavy keys, the
 //                      bucket numbering (light table L, heavy hash table H)
-//   hist     (all)     per-bucket totals of every subproblem
+//   hist     (all)     per-block bucket counts (rows of the count matrix)
+//   mscan    (all)     column scan of the count matrix, decoupled look-back
 //   scan     (CTA/sub) bucket starts; children for the next level, on-chip
 //                      base-case tasks, dovetail-merge zones (Alg. 2 step 3)
 //   scatter  (all)     Alg. 2 step 2: stable counting sort by bucket id;
-//                      per-tile warp ranking + decoupled look-back scan
-//   finish   (all)     base case on chip (stable LSD in shared memory) and
-//                      plain copies
+//                      per-tile warp ranking, staged bucket-ordered write-out
+//   finish   (all)     base case on chip (one counting pass over unique
+//                      (key, index) composites; stable LSD passes as the
+//                      fallback) and plain copies
 // After the last level, the dovetail merges (Alg. 3 semantics) run from the
 // deepest level up.  Every spin-wait is bounded by %globaltimer and latches
 // DTSORT_ERR_DEVICE_TIMEOUT instead of hanging.

@@ -19,7 +19,7 @@ struct Shape {
   static constexpr int FIN_CAP = (96 * 1024) / (2 * (KB + VB)) < CAP_MAX
                                       ? (96 * 1024) / (2 * (KB + VB)) : CAP_MAX;
   // base-case area: the two record buffers of the LSD passes, or the one-pass
-  // bins, placed composites and values (see fin_onepass)
+  // bins, placed composites and values (see fin_core)
   static constexpr int FIN_BYTES = 96 * 1024;
   static constexpr int FIN_IT = FIN_CAP / NT;           // base-case items / thread
   // largest bin sorted in place by its owner thread: without values a big
