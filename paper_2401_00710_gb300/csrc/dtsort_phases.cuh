@@ -1933,7 +1933,14 @@ __global__ void __launch_bounds__(NT, phase_min_blocks(PH))
   else if constexpr (PH == KP_SCATTER) phase_scatter<K, HV>(P, level, smem);
   else if constexpr (PH == KP_FINISH) {
     phase_finish<K, HV>(P, level, smem);
-    if (blockIdx.x == 0 && threadIdx.x == 0) c->levels_done = level + 1;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      c->levels_done = level + 1;
+      // a level without children ends the recursion: clear its own list too,
+      // so that a queued level two further down (same list parity) finds no
+      // subproblems instead of this level's (no phase of this level reads
+      // the list any more)
+      if (ld_cg64(&c->nseg[(level + 1) & 1]) == 0) c->nseg[level & 1] = 0;
+    }
   }
 }
 

@@ -64,6 +64,20 @@ def test_u32_kv_families(G, name):
     check(G, keys, vals)
 
 
+@pytest.mark.parametrize("dtype", [np.uint32, np.uint64])
+def test_queued_levels_beyond_the_recursion(G, dtype):
+    # narrow digits make the host queue three levels of phase launches for a
+    # uniform input of this size, while two distinct keys are both heavy at
+    # level 0: the queued levels 1 and 2 must find no subproblems
+    n = 3_000_017
+    keys = gen.keys(n, gen.DISTINCT, dtype, seed=6, p1=2)
+    vals = gen.iota(n, dtype)
+    G.set_options(gamma_max=4)
+    st = check(G, keys, vals)
+    assert st["status"] == 0
+    assert st["levels"] == 1
+
+
 def test_graph_transpose_edges(G):
     # a power-law edge list ordered by source, sorted stably by destination
     # (the transpose): each destination's sources stay in increasing order
