@@ -483,7 +483,9 @@ dtsort_status run_sort(dtsort_handle h, int op, void *keys, void *vals, const in
     case DTSORT_OP_U64: e = dts::launch_u64(P, grid, head, *ks, h->nsm, s); break;
     default: e = dts::launch_u64kv(P, grid, head, *ks, h->nsm, s); break;
   }
-  h->launches += 1 + (head > 0 ? 1 + 7 * (int64_t)head : 0);
+  // the persistent kernel; with queued levels also the seed, 7 phases and 2
+  // merge phases per level, and the statistics
+  h->launches += 1 + (head > 0 ? 2 + 9 * (int64_t)head : 0);
   return from_cuda(e);
 }
 

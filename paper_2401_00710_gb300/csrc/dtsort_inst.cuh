@@ -21,7 +21,7 @@ cudaError_t DTS_CAT(shape_, DTS_NAME)(KernelShape *out) {
   e = cudaFuncSetAttribute(dtsort_phase_kernel<DTS_K, DTS_HV>,
                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  const void *pk[8] = {
+  const void *pk[12] = {
       (const void *)dtsort_phase_one<DTS_K, DTS_HV, KP_SEED>,
       (const void *)dtsort_phase_one<DTS_K, DTS_HV, KP_SETUP>,
       (const void *)dtsort_phase_one<DTS_K, DTS_HV, KP_SAMPLE>,
@@ -29,8 +29,16 @@ cudaError_t DTS_CAT(shape_, DTS_NAME)(KernelShape *out) {
       (const void *)dtsort_phase_one<DTS_K, DTS_HV, KP_MSCAN>,
       (const void *)dtsort_phase_one<DTS_K, DTS_HV, KP_SCAN>,
       (const void *)dtsort_phase_one<DTS_K, DTS_HV, KP_SCATTER>,
-      (const void *)dtsort_phase_one<DTS_K, DTS_HV, KP_FINISH>};
-  for (int ph = 0; ph < 8; ++ph) {
+      (const void *)dtsort_phase_one<DTS_K, DTS_HV, KP_FINISH>,
+      nullptr,  // KP_CLOSE: inside the persistent kernel only
+      (const void *)dtsort_phase_one<DTS_K, DTS_HV, KP_MERGE_PREP>,
+      (const void *)dtsort_phase_one<DTS_K, DTS_HV, KP_MERGE>,
+      (const void *)dtsort_phase_one<DTS_K, DTS_HV, KP_STATS>};
+  for (int ph = 0; ph < 12; ++ph) {
+    if (!pk[ph]) {
+      out->phase_blocks[ph] = 0;
+      continue;
+    }
     const size_t sm = phase_smem_bytes<DTS_K, DTS_HV>(ph);
     e = cudaFuncSetAttribute(pk[ph], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
@@ -59,24 +67,27 @@ cudaError_t DTS_CAT(launch_, DTS_NAME)(const Params &P, int grid, int head, cons
                                        int nsm, cudaStream_t s) {
   const size_t smem = smem_bytes<DTS_K, DTS_HV>();
   cudaError_t e;
+  // one kernel per phase (attributes set by shape_), each with its own
+  // shared memory and as many CTAs as an SM holds of it
+  auto run = [&](int phase, int level, int g0, int prev) {
+    const int g = g0 == 1 ? 1 : nsm * (ks.phase_blocks[phase] > 0 ? ks.phase_blocks[phase] : 1);
+    const size_t smem = phase_smem_bytes<DTS_K, DTS_HV>(phase);
+    switch (phase) {
+      case KP_SEED: dtsort_phase_one<DTS_K, DTS_HV, KP_SEED><<<g, NT, smem, s>>>(P, level, prev); break;
+      case KP_SETUP: dtsort_phase_one<DTS_K, DTS_HV, KP_SETUP><<<g, NT, smem, s>>>(P, level, prev); break;
+      case KP_SAMPLE: dtsort_phase_one<DTS_K, DTS_HV, KP_SAMPLE><<<g, NT, smem, s>>>(P, level, prev); break;
+      case KP_HIST: dtsort_phase_one<DTS_K, DTS_HV, KP_HIST><<<g, NT, smem, s>>>(P, level, prev); break;
+      case KP_MSCAN: dtsort_phase_one<DTS_K, DTS_HV, KP_MSCAN><<<g, NT, smem, s>>>(P, level, prev); break;
+      case KP_SCAN: dtsort_phase_one<DTS_K, DTS_HV, KP_SCAN><<<g, NT, smem, s>>>(P, level, prev); break;
+      case KP_SCATTER: dtsort_phase_one<DTS_K, DTS_HV, KP_SCATTER><<<g, NT, smem, s>>>(P, level, prev); break;
+      case KP_MERGE_PREP: dtsort_phase_one<DTS_K, DTS_HV, KP_MERGE_PREP><<<g, NT, smem, s>>>(P, level, prev); break;
+      case KP_MERGE: dtsort_phase_one<DTS_K, DTS_HV, KP_MERGE><<<g, NT, smem, s>>>(P, level, prev); break;
+      case KP_STATS: dtsort_phase_one<DTS_K, DTS_HV, KP_STATS><<<g, NT, smem, s>>>(P, level, prev); break;
+      default: dtsort_phase_one<DTS_K, DTS_HV, KP_FINISH><<<g, NT, smem, s>>>(P, level, prev); break;
+    }
+    return cudaGetLastError();
+  };
   if (head > 0) {
-    // one kernel per phase (attributes set by shape_), each with its own
-    // shared memory and as many CTAs as an SM holds of it
-    auto run = [&](int phase, int level, int g0, int prev) {
-      const int g = g0 == 1 ? 1 : nsm * (ks.phase_blocks[phase] > 0 ? ks.phase_blocks[phase] : 1);
-      const size_t smem = phase_smem_bytes<DTS_K, DTS_HV>(phase);
-      switch (phase) {
-        case KP_SEED: dtsort_phase_one<DTS_K, DTS_HV, KP_SEED><<<g, NT, smem, s>>>(P, level, prev); break;
-        case KP_SETUP: dtsort_phase_one<DTS_K, DTS_HV, KP_SETUP><<<g, NT, smem, s>>>(P, level, prev); break;
-        case KP_SAMPLE: dtsort_phase_one<DTS_K, DTS_HV, KP_SAMPLE><<<g, NT, smem, s>>>(P, level, prev); break;
-        case KP_HIST: dtsort_phase_one<DTS_K, DTS_HV, KP_HIST><<<g, NT, smem, s>>>(P, level, prev); break;
-        case KP_MSCAN: dtsort_phase_one<DTS_K, DTS_HV, KP_MSCAN><<<g, NT, smem, s>>>(P, level, prev); break;
-        case KP_SCAN: dtsort_phase_one<DTS_K, DTS_HV, KP_SCAN><<<g, NT, smem, s>>>(P, level, prev); break;
-        case KP_SCATTER: dtsort_phase_one<DTS_K, DTS_HV, KP_SCATTER><<<g, NT, smem, s>>>(P, level, prev); break;
-        default: dtsort_phase_one<DTS_K, DTS_HV, KP_FINISH><<<g, NT, smem, s>>>(P, level, prev); break;
-      }
-      return cudaGetLastError();
-    };
     if ((e = run(KP_SEED, 0, grid, -1)) != cudaSuccess) return e;
     for (int l = 0; l < head; ++l) {
       if ((e = run(KP_SETUP, l, 1, l == 0 ? PH_SETUP : PH_FINISH)) != cudaSuccess ||
@@ -93,7 +104,16 @@ cudaError_t DTS_CAT(launch_, DTS_NAME)(const Params &P, int grid, int head, cons
   Params copy = P;
   int lev0 = head;
   void *args[] = {&copy, &lev0};
-  return cudaLaunchCooperativeKernel((const void *)fn, dim3(grid), dim3(NT), args, smem, s);
+  e = cudaLaunchCooperativeKernel((const void *)fn, dim3(grid), dim3(NT), args, smem, s);
+  if (e != cudaSuccess || head == 0) return e;
+  // the queued levels' dovetail merges, deepest first (each returns at once
+  // when its level has no merge zone), then the statistics
+  for (int l = head - 1; l >= 0; --l) {
+    if ((e = run(KP_MERGE_PREP, l, grid, PH_MERGE)) != cudaSuccess ||
+        (e = run(KP_MERGE, l, grid, PH_MERGE)) != cudaSuccess)
+      return e;
+  }
+  return run(KP_STATS, 0, 1, PH_MERGE);
 }
 
 // One launch per phase; the host reads the control block between levels.

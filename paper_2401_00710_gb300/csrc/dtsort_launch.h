@@ -17,7 +17,7 @@ struct KernelShape {
   int ch;    // rows per look-back chunk
   size_t smem;
   int blocks_per_sm;
-  int phase_blocks[8];  // CTAs per SM of each single-phase kernel (queued levels)
+  int phase_blocks[12];  // CTAs per SM of each single-phase kernel (by phase id)
 };
 
 #define DTS_DECLARE(NAME)                                                      \

@@ -118,6 +118,10 @@ constexpr size_t phase_smem_bytes(int ph) {
     case 5: return scan;                       // KP_SCAN
     case 0:                                    // KP_SEED
     case 1: return 8 * (NWARP + 1) + 256;      // KP_SETUP
+    case 9:                                    // KP_MERGE_PREP
+    case 10:                                   // KP_MERGE: heavy runs, warp sums
+      return 3 * (16 + 8 * (HASH_HW / 2 + 1)) + 16 + 8 * (NWARP + 1) + 16 + sizeof(MZone) + 256;
+    case 11: return 256;                       // KP_STATS
     default: return smem_bytes<K, HV>();       // scatter, base case
   }
 }
@@ -1787,7 +1791,8 @@ __device__ __forceinline__ void run_phase(const Params &P, int phase, int level)
 // decided alike by every CTA from the control block after a grid barrier.
 // Returns KP_DONE after the last merge.
 constexpr int KP_DONE = -1;
-__device__ __forceinline__ int next_phase(const Params &P, int phase, int &level) {
+__device__ __forceinline__ int next_phase(const Params &P, int phase, int &level,
+                                          int mfloor) {
   Ctl *c = P.ctl;
   const bool err = *(volatile int *)&c->err_snap != 0;
   switch (phase) {
@@ -1811,10 +1816,12 @@ __device__ __forceinline__ int next_phase(const Params &P, int phase, int &level
     }
     case KP_CLOSE:
     case KP_MERGE: {
-      // merges run from the deepest level up; levels without zones are skipped
+      // merges run from the deepest level up to mfloor (the levels above it
+      // merge in launches of their own after this kernel); levels without
+      // zones are skipped
       int l = phase == KP_CLOSE ? *(volatile int *)&c->nlevels - 1 : level - 1;
-      while (l >= 0 && ld_cg64(&c->lvl_zone[l + 1]) == ld_cg64(&c->lvl_zone[l])) --l;
-      if (l < 0 || err) return KP_DONE;
+      while (l >= mfloor && ld_cg64(&c->lvl_zone[l + 1]) == ld_cg64(&c->lvl_zone[l])) --l;
+      if (l < mfloor || err) return KP_DONE;
       level = l;
       return KP_MERGE_PREP;
     }
@@ -1839,8 +1846,10 @@ __device__ __forceinline__ int phase_kind(int phase) {
 }
 
 // The persistent kernel.  lev0 = 0: the whole sort from the seed phase.
-// lev0 > 0: the first levels already ran as separate phase launches; start
-// at the first level they did not finish (or close if nothing is left).
+// lev0 > 0: the first lev0 levels are queued as separate phase launches;
+// start at the first level they did not finish (or close if nothing is left)
+// and merge only the levels from lev0 down: the queued levels' merges and the
+// statistics are launches of their own after this kernel.
 template <typename K, bool HV>
 __global__ void __launch_bounds__(NT, 2) dtsort_kernel(const __grid_constant__ Params P,
                                                        int lev0) {
@@ -1869,14 +1878,16 @@ __global__ void __launch_bounds__(NT, 2) dtsort_kernel(const __grid_constant__ P
     run_phase<K, HV>(P, phase, level);
     grid_sync(P);
     tick(P, phase_kind(phase));
-    const int next = next_phase(P, phase, level);
+    const int next = next_phase(P, phase, level, lev0);
     if (threadIdx.x == 0) {
       *(volatile int *)&st_phase = next;
       *(volatile int *)&st_level = level;
     }
     __syncthreads();
   }
-  write_stats(P, c->t_begin);
+  // after queued levels, their merges and the statistics follow as launches
+  // of their own
+  if (lev0 == 0) write_stats(P, c->t_begin);
 }
 
 // One phase per launch.  guard = 1 (launches queued without the host reading
@@ -1915,8 +1926,20 @@ template <typename K, bool HV, int PH>
 __global__ void __launch_bounds__(NT, phase_min_blocks(PH))
     dtsort_phase_one(const __grid_constant__ Params P, int level, int prev_kind) {
   Ctl *c = P.ctl;
+  if (PH == KP_STATS) {  // after an error too: the status goes out with them
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      if (prev_kind >= 0) tick(P, prev_kind);
+      write_stats(P, c->t_begin);
+    }
+    return;
+  }
   if (*(volatile int *)&c->error) return;
   if (PH >= KP_SETUP && PH <= KP_FINISH && level > 0 && ld_cg64(&c->nseg[level & 1]) == 0)
+    return;
+  // a queued merge of a level without zones (or not reached) returns at once
+  if ((PH == KP_MERGE_PREP || PH == KP_MERGE) &&
+      (level >= *(volatile int *)&c->nlevels ||
+       ld_cg64(&c->lvl_zone[level + 1]) == ld_cg64(&c->lvl_zone[level])))
     return;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     if (PH == KP_SEED) c->t_last = c->t_begin = gtimer();
@@ -1931,6 +1954,8 @@ __global__ void __launch_bounds__(NT, phase_min_blocks(PH))
   else if constexpr (PH == KP_MSCAN) phase_mscan<K, HV>(P, level, smem);
   else if constexpr (PH == KP_SCAN) phase_scan<K, HV>(P, level, smem);
   else if constexpr (PH == KP_SCATTER) phase_scatter<K, HV>(P, level, smem);
+  else if constexpr (PH == KP_MERGE_PREP) phase_merge_prep<K, HV>(P, level, smem);
+  else if constexpr (PH == KP_MERGE) phase_merge<K, HV>(P, level, smem);
   else if constexpr (PH == KP_FINISH) {
     phase_finish<K, HV>(P, level, smem);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
