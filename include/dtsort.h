@@ -109,8 +109,8 @@ typedef struct {
   int32_t launch_mode;       /* 0 (default): the levels a uniformly
                                 distributed input of n keys needs (n = the
                                 total for a segmented call, which bounds every
-                                array), and two more, run as one launch per
-                                phase, queued
+                                array), and from 2^26 records on two more,
+                                run as one launch per phase, queued
                                 without host synchronisation (each phase checks
                                 on the device whether it has work), then one
                                 persistent cooperative launch takes any further

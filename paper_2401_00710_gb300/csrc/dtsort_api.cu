@@ -469,14 +469,17 @@ dtsort_status run_sort(dtsort_handle h, int op, void *keys, void *vals, const in
     h->launches += cnt;
     return from_cuda(e);
   }
-  // the levels a uniform input of n keys needs, and two more for skewed
-  // inputs, run as separate phase launches, the rest (if any) in the
-  // persistent kernel; for a segmented call n (the total) bounds every
+  // the levels a uniform input of n keys needs, and for n >= 2^26 two more
+  // for skewed inputs, run as separate phase launches, the rest (if any) in
+  // the persistent kernel; for a segmented call n (the total) bounds every
   // array's size.  A queued level without work returns at once on the device
-  // (two unused levels cost nothing measurable on uniform keys; skewed inputs
-  // gain 4-9%: their deeper levels then run in the per-phase kernels, which
-  // spill less than the persistent one)
-  const int head = h->opt.launch_mode == 0 ? predict_levels(n, 8 * kb, o, L.target) + 2 : 0;
+  // (two unused levels cost nothing measurable on 10^9 uniform keys; skewed
+  // inputs gain 4-9%, their deeper levels then running in the per-phase
+  // kernels, which spill less than the persistent one; below 2^26 records the
+  // sort is launch-bound and the empty launches would show)
+  const int extra = n >= ((int64_t)1 << 26) ? 2 : 0;
+  const int head =
+      h->opt.launch_mode == 0 ? predict_levels(n, 8 * kb, o, L.target) + extra : 0;
   switch (op) {
     case DTSORT_OP_U32: e = dts::launch_u32(P, grid, head, *ks, h->nsm, s); break;
     case DTSORT_OP_U32_KV: e = dts::launch_u32kv(P, grid, head, *ks, h->nsm, s); break;
