@@ -430,9 +430,10 @@ def run_ours(args):
                      "traffic": dram_traffic(args.op, args.dist, n)
                      if args.bucketing == "digit" else None,
                      "peak_kind": peak_kind, "bytes_per_record": B_ALG[args.op],
-                     "kernel": "one sort: the per-phase launches of the predicted levels "
-                               "(dts::dtsort_phase_kernel) + the persistent dts::dtsort_kernel; "
-                               "achieved = algorithmic bytes / CUDA-event time of the sort"},
+                     "kernel": "one sort: the queued per-phase launches (dts::dtsort_phase_one: "
+                               "levels, their merges, statistics) + the persistent "
+                               "dts::dtsort_kernel; achieved = algorithmic bytes / CUDA-event "
+                               "time of the sort"},
         "gpu_launches": args.steps * stats["kernel_launches"],
         "clocks": clk.summary(),
         "e2e": e2e,
