@@ -1329,8 +1329,8 @@ __device__ void phase_finish(const Params &P, int level, unsigned char *smem) {
     K *kd = kdst + tk.start;
     K *vd = HV ? vdst + tk.start : nullptr;
     // composites over the task's own key range [base, base + 2^hi) when they
-    // fit; the bins are counted while the records are loaded into registers
-    // (item j of thread t is record j * NT + t)
+    // fit; the bins are counted right after the records are loaded into
+    // registers (item j of thread t is record j * NT + t)
     const int hi = tk.hi;
     const int ct = hi + IB <= 32 ? 1 : (WIDE && hi + IB <= 64 ? 2 : 0);
     const int fb0 = min(max(bitlen64((uint64_t)(n - 1)) + 1, 9), ct == 2 ? FBM64 : FBM32);
