@@ -12,12 +12,15 @@ struct Shape {
   static constexpr int VB = HV ? (int)sizeof(K) : 0;
   static constexpr int ITEMS = KB == 4 ? 16 : 8;        // scatter items / thread
   static constexpr int TILE = NT * ITEMS;
-  // 32-bit keys: 9 items per thread (a uniform 10^9-record sort's buckets
-  // hold about 3,800 records: 8 live rounds of the unrolled loops instead of
-  // 8 of 12; measured 6.65 -> 6.43 ms for the base case)
-  static constexpr int CAP_MAX = KB == 4 ? 9 * NT : 6144;
-  static constexpr int FIN_CAP = (96 * 1024) / (2 * (KB + VB)) < CAP_MAX
-                                      ? (96 * 1024) / (2 * (KB + VB)) : CAP_MAX;
+  // 9 items per thread with values or 32-bit keys (a uniform 10^9-record
+  // sort's buckets hold about 3,800 records: two levels for 64-bit key/value
+  // pairs too, and 8 live rounds of the unrolled loops instead of 8 of 12 for
+  // 32-bit keys), 12 for 64-bit keys alone.  The LSD fallback's two key and
+  // two 16-bit index buffers must fit the base-case area.
+  static constexpr int CAP_MAX = (KB == 4 || HV) ? 9 * NT : 12 * NT;
+  static constexpr int FIN_LSD_REC = KB + (HV ? 2 : 0);  // LSD bytes per record
+  static constexpr int FIN_CAP = (96 * 1024) / (2 * FIN_LSD_REC) < CAP_MAX
+                                      ? (96 * 1024) / (2 * FIN_LSD_REC) : CAP_MAX;
   // base-case area: the two record buffers of the LSD passes, or the one-pass
   // bins, placed composites and values (see fin_core)
   static constexpr int FIN_BYTES = 96 * 1024;
@@ -1051,13 +1054,16 @@ struct FinArea {
   static constexpr int FBM = fin_fb<K, HV, CT>();
   static constexpr int PC_OFF = (4 * ((1 << FBM) + NT) + 15) & ~15;
   static constexpr int V_OFF = PC_OFF + ((int)((sizeof(CT) * Shape<K, HV>::FIN_CAP + 15) & ~15));
+  static_assert(V_OFF + Shape<K, HV>::VB * Shape<K, HV>::FIN_CAP <= Shape<K, HV>::FIN_BYTES,
+                "bins, composites and values fit the base-case area");
 };
 
 // Histogram of a task's records (item j of thread t is record i = j NT + t,
-// keys in [kb, kb + 2^bits)) on bins fin_bin(key - kb, i, ksh, ish), and the
-// values in input order; the bins must be zero.
+// keys in [kb, kb + 2^bits), held in registers) on bins fin_bin(key - kb, i,
+// ksh, ish), and the values (read again from vs) in input order; the bins
+// must be zero.
 template <typename K, bool HV, typename CT>
-__device__ __forceinline__ void fin_hist(const Rec<K, HV> (&rr)[Shape<K, HV>::FIN_IT], int n,
+__device__ __forceinline__ void fin_hist(const K (&rk)[Shape<K, HV>::FIN_IT], const K *vs, int n,
                                          int R, K kb, int ksh, int ish, int psh,
                                          unsigned char *region) {
   using S = Shape<K, HV>;
@@ -1068,15 +1074,16 @@ __device__ __forceinline__ void fin_hist(const Rec<K, HV> (&rr)[Shape<K, HV>::FI
   for (int j = 0; j < S::FIN_IT; ++j) {
     const int i = j * NT + threadIdx.x;
     if (j < R && i < n) {
-      if constexpr (HV) vst[i] = rr[j].v;
-      const unsigned b = fin_bin<K, HV>(key_off<K>(rr[j].k, kb), i, ksh, ish);
+      if constexpr (HV) vst[i] = ld_key<K>(vs + i);
+      const unsigned b = fin_bin<K, HV>(key_off<K>(rk[j], kb), i, ksh, ish);
       atomicAdd(&bins[b + (b >> psh)], 1u);
     }
   }
 }
 
-// One-pass base case of a task of n <= FIN_CAP records held in registers
-// (item j of thread t is record i = j NT + t), keys in [kb, kb + 2^bits),
+// One-pass base case of a task of n <= FIN_CAP records whose keys are held in
+// registers (item j of thread t is record i = j NT + t), keys in
+// [kb, kb + 2^bits), values in the input-order copy,
 // after fin_hist has counted its 2^fb bins (fin_bin with ksh, ish).  Each
 // record is the composite c = (key - kb) << FIN_IB | i (without values
 // c = key - kb): with values the composites are distinct and their order is
@@ -1090,7 +1097,7 @@ __device__ __forceinline__ void fin_hist(const Rec<K, HV> (&rr)[Shape<K, HV>::FI
 // memory, when a bin holds more than FIN_CMAX records.  Barriers: 4 (1 when
 // it returns false).
 template <typename K, bool HV, typename CT>
-__device__ __forceinline__ bool fin_core(const Rec<K, HV> (&rr)[Shape<K, HV>::FIN_IT], int n,
+__device__ __forceinline__ bool fin_core(const K (&rk)[Shape<K, HV>::FIN_IT], int n,
                                          int R, K kb, int fb, int ksh, int ish,
                                          unsigned char *region,
                                          unsigned *wsum, unsigned *cmax, K *kd, K *vd,
@@ -1147,9 +1154,9 @@ __device__ __forceinline__ bool fin_core(const Rec<K, HV> (&rr)[Shape<K, HV>::FI
   for (int j = 0; j < S::FIN_IT; ++j) {
     const int i = j * NT + threadIdx.x;
     if (j < R && i < n) {
-      const unsigned b = fin_bin<K, HV>(key_off<K>(rr[j].k, kb), i, ksh, ish);
+      const unsigned b = fin_bin<K, HV>(key_off<K>(rk[j], kb), i, ksh, ish);
       const unsigned p = atomicAdd(&bins[b + (b >> psh)], 1u);
-      if (p < (unsigned)n) pc[p] = comp(rr[j].k, i);
+      if (p < (unsigned)n) pc[p] = comp(rk[j], i);
       else bad = 1u + p;
     }
   }
@@ -1208,11 +1215,13 @@ __device__ void phase_finish(const Params &P, int level, unsigned char *smem) {
   using S = Shape<K, HV>;
   Ctl *c = P.ctl;
   const int64_t ntasks = min(ld_cg64(&c->ntasks), (long long)P.tmax);
-  using RecT = Rec<K, HV>;
   Carve cv;
   unsigned char *region = cv.take<unsigned char>(S::FIN_BYTES);
-  RecT *ra = (RecT *)region;  // LSD passes: two record buffers
-  RecT *rb = ra + S::FIN_CAP;
+  // LSD passes: two key buffers and (with values) two 16-bit index buffers
+  K *lka = (K *)region;
+  K *lkb = lka + S::FIN_CAP;
+  uint16_t *lia = (uint16_t *)(lkb + S::FIN_CAP);
+  uint16_t *lib = lia + S::FIN_CAP;
   uint16_t *wcnt = cv.take<uint16_t>(NWARP * FIN_NB);
   unsigned *dcnt = cv.take<unsigned>(FIN_NB);
   unsigned *doff = cv.take<unsigned>(FIN_NB);
@@ -1226,8 +1235,9 @@ __device__ void phase_finish(const Params &P, int level, unsigned char *smem) {
   K *kmax_sh = cv.take<K>(2);
   unsigned *cmax_sh = cv.take<unsigned>(3);
   int *flag_sh = cv.take<int>(1);
-  static_assert(2 * sizeof(RecT) * S::FIN_CAP <= (size_t)S::FIN_BYTES, "LSD buffers fit");
-  static_assert(sizeof(RecT) * S::FIN_CAP >= 4 * NWARP * FIN_NB, "slots fit in a buffer");
+  static_assert(2 * (size_t)S::FIN_LSD_REC * S::FIN_CAP <= (size_t)S::FIN_BYTES,
+                "LSD buffers fit");
+  static_assert(sizeof(K) * S::FIN_CAP >= 4 * NWARP * FIN_NB, "slots fit in a key buffer");
   static_assert(S::FIN_CAP <= (1 << FIN_IB), "indices fit in FIN_IB bits");
   constexpr int IB = HV ? FIN_IB : 0;
   constexpr bool WIDE = sizeof(K) == 8 || HV;  // 64-bit composites can be needed
@@ -1341,14 +1351,19 @@ __device__ void phase_finish(const Params &P, int level, unsigned char *smem) {
     unsigned *bins = (unsigned *)region;
     K *vst0 = (K *)(region + (ct == 2 ? FinArea<K, HV, uint64_t>::V_OFF
                                       : FinArea<K, HV, uint32_t>::V_OFF));
-    RecT rr[S::FIN_IT];
+    // keys into registers; values copied asynchronously straight into the
+    // input-order copy (read from global memory again by the rare paths that
+    // need them elsewhere)
+    K rk[S::FIN_IT];
 #pragma unroll
     for (int j = 0; j < S::FIN_IT; ++j) {
       if (j < R) {
         const int i = j * NT + threadIdx.x;
         if (i < n) {
-          rr[j].k = ld_key<K>(ks + i);
-          if constexpr (HV) rr[j].v = ld_key<K>(vs + i);
+          rk[j] = ld_key<K>(ks + i);
+          if constexpr (HV) {
+            if (ct) cp_async_el<K>(vst0 + i, vs + i);
+          }
         }
       }
     }
@@ -1357,16 +1372,16 @@ __device__ void phase_finish(const Params &P, int level, unsigned char *smem) {
       for (int j = 0; j < S::FIN_IT; ++j) {
         const int i = j * NT + threadIdx.x;
         if (j < R && i < n) {
-          const KOff<K> dk = key_off<K>(rr[j].k, kb0);
+          const KOff<K> dk = key_off<K>(rk[j], kb0);
           if (hi < 8 * (int)sizeof(K) && (dk >> hi) != 0) {
             bad = 1u + (unsigned)i;  // a key outside the task's range
           } else {
-            if constexpr (HV) vst0[i] = rr[j].v;
             const unsigned b = fin_bin<K, HV>(dk, i, ksh0, ish0);
             atomicAdd(&bins[b + (b >> psh0)], 1u);
           }
         }
       }
+      if constexpr (HV) cp_async_wait_all();  // the values, before the barrier
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -1378,11 +1393,11 @@ __device__ void phase_finish(const Params &P, int level, unsigned char *smem) {
     // words of the bin area this task may leave nonzero (cleared at its end)
     int dirty = ct ? (1 << fb0) + NT : 0;
     if (ct == 1) {
-      done = fin_core<K, HV, uint32_t>(rr, n, R, kb0, fb0, ksh0, ish0, region, wsum,
+      done = fin_core<K, HV, uint32_t>(rk, n, R, kb0, fb0, ksh0, ish0, region, wsum,
                                        &cmax_sh[par], kd, vd, bad);
     } else if (ct == 2) {
       if constexpr (WIDE)
-        done = wide = fin_core<K, HV, uint64_t>(rr, n, R, kb0, fb0, ksh0, ish0, region, wsum,
+        done = wide = fin_core<K, HV, uint64_t>(rk, n, R, kb0, fb0, ksh0, ish0, region, wsum,
                                                 &cmax_sh[par], kd, vd, bad);
     }
     if (!done) {
@@ -1393,8 +1408,8 @@ __device__ void phase_finish(const Params &P, int level, unsigned char *smem) {
       for (int j = 0; j < S::FIN_IT; ++j) {
         const int i = j * NT + threadIdx.x;
         if (j < R && i < n) {
-          kmn = rr[j].k < kmn ? rr[j].k : kmn;
-          kmx = rr[j].k > kmx ? rr[j].k : kmx;
+          kmn = rk[j] < kmn ? rk[j] : kmn;
+          kmx = rk[j] > kmx ? rk[j] : kmx;
         }
       }
       kmn = warp_min(kmn);
@@ -1419,8 +1434,8 @@ __device__ void phase_finish(const Params &P, int level, unsigned char *smem) {
         for (int j = 0; j < S::FIN_IT; ++j) {
           const int i = j * NT + threadIdx.x;
           if (j < R && i < n) {
-            kd[i] = rr[j].k;
-            if constexpr (HV) vd[i] = rr[j].v;
+            kd[i] = rk[j];
+            if constexpr (HV) vd[i] = ld_key<K>(vs + i);
           }
         }
         done = true;
@@ -1431,15 +1446,15 @@ __device__ void phase_finish(const Params &P, int level, unsigned char *smem) {
         const int ksh1 = bl > fb1 ? bl - fb1 : 0;
         const int ish1 = HV && fb1 > bl ? fb1 - bl : 0;
         if (ct1 == 1) {
-          fin_hist<K, HV, uint32_t>(rr, n, R, kmin, ksh1, ish1, fb1 - 9, region);
+          fin_hist<K, HV, uint32_t>(rk, vs, n, R, kmin, ksh1, ish1, fb1 - 9, region);
           __syncthreads();
-          done = fin_core<K, HV, uint32_t>(rr, n, R, kmin, fb1, ksh1, ish1, region, wsum,
+          done = fin_core<K, HV, uint32_t>(rk, n, R, kmin, fb1, ksh1, ish1, region, wsum,
                                            &cmax_sh[2], kd, vd, bad);
         } else if (ct1 == 2) {
           if constexpr (WIDE) {
-            fin_hist<K, HV, uint64_t>(rr, n, R, kmin, ksh1, ish1, fb1 - 9, region);
+            fin_hist<K, HV, uint64_t>(rk, vs, n, R, kmin, ksh1, ish1, fb1 - 9, region);
             __syncthreads();
-            done = wide = fin_core<K, HV, uint64_t>(rr, n, R, kmin, fb1, ksh1, ish1, region,
+            done = wide = fin_core<K, HV, uint64_t>(rk, n, R, kmin, fb1, ksh1, ish1, region,
                                                     wsum, &cmax_sh[2], kd, vd, bad);
           }
         }
@@ -1447,16 +1462,20 @@ __device__ void phase_finish(const Params &P, int level, unsigned char *smem) {
     }
     if (!done) {
       // a bin with many equal-prefix keys: stable LSD passes over the task's
-      // hi bits
+      // hi bits on (key, original index), the values gathered at the end
       my_lsd += 1;
       dirty = ZFULL;
 #pragma unroll
       for (int j = 0; j < S::FIN_IT; ++j) {
         const int i = j * NT + threadIdx.x;
-        if (j < R && i < n) ra[i] = rr[j];
+        if (j < R && i < n) {
+          lka[i] = rk[j];
+          if constexpr (HV) lia[i] = (uint16_t)i;
+        }
       }
       __syncthreads();
-      RecT *rin = ra, *rout = rb;
+      K *kin = lka, *kout = lkb;
+      uint16_t *iin = lia, *iout = lib;
       const int passes = (tk.hi + FIN_DIG - 1) / FIN_DIG;
       // every warp ranks R consecutive rounds of 32 items (warp w covers
       // [32 R w, 32 R (w+1)) of the current order), R as small as n allows
@@ -1464,7 +1483,7 @@ __device__ void phase_finish(const Params &P, int level, unsigned char *smem) {
         const int shift = q * FIN_DIG;
         const int bits = tk.hi - shift < FIN_DIG ? tk.hi - shift : FIN_DIG;
         const unsigned dmask = (1u << bits) - 1u;
-        unsigned *fslots = (unsigned *)rout;  // rout is free until the scatter
+        unsigned *fslots = (unsigned *)kout;  // kout is free until the scatter
         {
           uint4 *z = (uint4 *)wcnt;
           for (int i = threadIdx.x; i < NWARP * FIN_NB * 2 / 16; i += NT) z[i] = make_uint4(0, 0, 0, 0);
@@ -1480,7 +1499,7 @@ __device__ void phase_finish(const Params &P, int level, unsigned char *smem) {
           dr[j] = 0xFFFFFFFFu;
           if (j < R && w * 32 * R + j * 32 < n) {  // warp-uniform
             unsigned d = 1u << FIN_DIG;  // dummy digit
-            if (i < n) d = (unsigned)(((uint64_t)rin[i].k - tk.base) >> shift) & dmask;
+            if (i < n) d = (unsigned)(((uint64_t)kin[i] - tk.base) >> shift) & dmask;
             const unsigned r = warp_rank_slots(d, myfs, mywc);
             dr[j] = (d << 16) | r;
           }
@@ -1518,18 +1537,41 @@ __device__ void phase_finish(const Params &P, int level, unsigned char *smem) {
               bad = 1u + pp;
               continue;
             }
-            rout[pp] = rin[i];
+            kout[pp] = kin[i];
+            if constexpr (HV) iout[pp] = iin[i];
           }
         }
         __syncthreads();
-        RecT *t_ = rin;
-        rin = rout;
-        rout = t_;
+        K *tk_ = kin;
+        kin = kout;
+        kout = tk_;
+        uint16_t *ti_ = iin;
+        iin = iout;
+        iout = ti_;
       }
-      for (int i = threadIdx.x; i < n; i += NT) {
-        const RecT x = rin[i];
-        kdst[tk.start + i] = x.k;
-        if constexpr (HV) vdst[tk.start + i] = x.v;
+      // the values by original index, all read before any is written (a
+      // task may sort in place: source and destination the same buffer)
+      K vg[S::FIN_IT];
+      if constexpr (HV) {
+#pragma unroll
+        for (int j = 0; j < S::FIN_IT; ++j) {
+          const int i = j * NT + threadIdx.x;
+          vg[j] = (K)0;
+          if (j < R && i < n) {
+            const unsigned src = iin[i];
+            if (src < (unsigned)n) vg[j] = ld_key<K>(vsrc + tk.start + src);
+            else bad = 1u + src;
+          }
+        }
+        __syncthreads();
+      }
+#pragma unroll
+      for (int j = 0; j < S::FIN_IT; ++j) {
+        const int i = j * NT + threadIdx.x;
+        if (j < R && i < n) {
+          kdst[tk.start + i] = kin[i];
+          if constexpr (HV) vdst[tk.start + i] = vg[j];
+        }
       }
       __syncthreads();
     }

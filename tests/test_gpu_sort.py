@@ -143,6 +143,31 @@ def test_base_case_ties(G, mult, dtype):
         check(G, keys, None)
 
 
+@pytest.mark.parametrize("dtype", [np.uint32, np.uint64])
+def test_in_place_lsd_fallback(G, dtype):
+    # a base case sorted in place (one sort below the capacity; segments of a
+    # batch) whose tied keys overflow a bin, so that the LSD passes run and
+    # gather the values by original index from the buffer they overwrite
+    rs = np.random.RandomState(11)
+    for n in (300, 3000, 4607):
+        keys = gen.family("uniform", n, dtype, seed=n)
+        keys[rs.permutation(n)[: n // 2]] = keys[0]
+        vals = gen.iota(n, dtype)
+        check(G, keys, vals)
+        assert G.stats()["finisher_lsd_tasks"] >= 1
+    sizes = [50 + (37 * s) % 4000 for s in range(64)]
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    keys = gen.family("uniform", int(off[-1]), dtype, seed=12)
+    for s in range(64):
+        a, b = off[s], off[s + 1]
+        keys[a + rs.permutation(b - a)[: (b - a) // 2]] = keys[a]
+    vals = gen.iota(len(keys), dtype)
+    gk, gv = G.sort(keys, vals, off)
+    ek, ev = oracle.stable_sort_segmented(keys, vals, off)
+    gpu_util.assert_same(gk, gv, ek, ev)
+    assert G.stats()["finisher_lsd_tasks"] >= 1
+
+
 def test_n_zero_is_noop(G):
     keys = np.zeros(0, dtype=np.uint32)
     st = G.launch(None, None, 0, dts.DTSORT_OP_U32_KV)
