@@ -70,6 +70,9 @@ def parse():
                     help="run the autotuner on the workload first and use its choice")
     ap.add_argument("--heavy", default="on", choices=["on", "off"],
                     help="off: no heavy-key detection (the paper's 'Plain' ablation)")
+    ap.add_argument("--merge", default="dovetail", choices=["dovetail", "generic"],
+                    help="generic: merge-path merging of the heavy zones instead of "
+                         "dovetail merging (the paper's merge ablation)")
     return ap.parse_args()
 
 
@@ -310,13 +313,15 @@ def run_ours(args):
           "u64kv": dts.DTSORT_OP_U64_KV, "u64": dts.DTSORT_OP_U64}[args.op]
     h = dts.dtsort_create(local)
     if (args.launch_mode or args.bucketing != "digit" or args.block_tiles or args.gamma_max or
-            args.capacity or args.heavy == "off"):
+            args.capacity or args.heavy == "off" or args.merge != "dovetail"):
         o = dts.dtsort_get_options(h)
         o.heavy_detection = -1 if args.heavy == "off" else 0
         o.launch_mode = args.launch_mode
         o.block_tiles = args.block_tiles
         o.gamma_max = args.gamma_max
         o.finisher_capacity = args.capacity
+        o.merge = (dts.DTSORT_MERGE_GENERIC if args.merge == "generic"
+                   else dts.DTSORT_MERGE_DOVETAIL)
         o.bucketing = {"digit": dts.DTSORT_BUCKETING_DIGIT,
                        "learned": dts.DTSORT_BUCKETING_LEARNED,
                        "learned-always": dts.DTSORT_BUCKETING_LEARNED_ALWAYS}[args.bucketing]
@@ -411,14 +416,16 @@ def run_ours(args):
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": args.op, "data": "synthetic",
-        "config": {"workload": "stable sort, %s, n=%d, keys %s seed %d, values = %s%s%s"
+        "config": {"workload": "stable sort, %s, n=%d, keys %s seed %d, values = %s%s%s%s"
                                % (args.op, n, args.dist, args.seed,
                                   "the edges' sources (graph transpose of a power-law "
                                   "edge list over 2^26 vertices)" if args.dist == "edges"
                                   else "index",
                                   "" if args.bucketing == "digit"
                                   else ", bucketing " + args.bucketing,
-                                  ", heavy-key detection off" if args.heavy == "off" else ""),
+                                  ", heavy-key detection off" if args.heavy == "off" else "",
+                                  ", generic merge-path merging" if args.merge == "generic"
+                                  else ""),
                    "n": n, "dist": args.dist,
                    "l2": ("inputs %.1f GB per step >> L2 (129 MB)" % (rec_bytes * n / 1e9)
                           if rec_bytes * n > 4 * 129e6 else

@@ -83,6 +83,19 @@ typedef enum {
   DTSORT_BUCKETING_LEARNED_ALWAYS = 2  /* the learned zones without the estimate */
 } dtsort_bucketing;
 
+/* Merging of a zone's sorted light bucket with its heavy buckets (Sec. 4).
+ * Both give the same output. */
+typedef enum {
+  DTSORT_MERGE_DOVETAIL = 0, /* Alg. 3: every record's position in closed
+                                form from the heavy buckets' sizes and one
+                                binary search per heavy key; no key compares */
+  DTSORT_MERGE_GENERIC = 1   /* a generic stable merge of the light bucket
+                                with the heavy buckets' concatenation: merge
+                                path, splitters found by key comparisons (the
+                                paper's comparison against a standard
+                                parallel merge) */
+} dtsort_merge;
+
 typedef struct dtsort_handle_s *dtsort_handle;
 
 /* Tuning knobs.  Zero fields mean "default" (or "autotuned" where autotune is
@@ -123,7 +136,9 @@ typedef struct {
   int32_t block_tiles;       /* rows of the per-level count matrix cover
                                 block_tiles tiles of the scatter (8K 32-bit or
                                 4K 64-bit keys each); 1..8, default 8 */
-  int32_t reserved[4];
+  int32_t merge;             /* dtsort_merge: how each heavy zone's runs are
+                                merged (default DOVETAIL) */
+  int32_t reserved[3];
 } dtsort_options;
 
 /* Statistics of the last completed sort on this handle (read after sync). */

@@ -25,6 +25,7 @@ DTSORT_ERR_INTERNAL = 6
 
 DTSORT_OP_U32, DTSORT_OP_U32_KV, DTSORT_OP_U64, DTSORT_OP_U64_KV = 0, 1, 2, 3
 DTSORT_BUCKETING_DIGIT, DTSORT_BUCKETING_LEARNED, DTSORT_BUCKETING_LEARNED_ALWAYS = 0, 1, 2
+DTSORT_MERGE_DOVETAIL, DTSORT_MERGE_GENERIC = 0, 1
 
 # C symbols declared in include/dtsort.h
 EXPORTED = [
@@ -63,7 +64,8 @@ class dtsort_options(ctypes.Structure):
                 ("debug_fault", ctypes.c_int32),
                 ("launch_mode", ctypes.c_int32),
                 ("block_tiles", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 4)]
+                ("merge", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 3)]
 
 
 class dtsort_stats(ctypes.Structure):

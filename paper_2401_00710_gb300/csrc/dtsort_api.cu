@@ -39,7 +39,7 @@ struct Layout {
 };
 
 struct Opts {
-  int gamma_max, cap, heavy_on, sample_factor, debug_fault, blk_tiles;
+  int gamma_max, cap, heavy_on, merge_generic, sample_factor, debug_fault, blk_tiles;
   uint64_t seed;
   unsigned long long wait_ns;
 };
@@ -87,6 +87,7 @@ Opts effective(const dtsort_options &o, const KernelShape &ks, int64_t nsegs = 1
   r.cap = (o.finisher_capacity > 0 && o.finisher_capacity < ks.fin_cap) ? o.finisher_capacity
                                                                         : ks.fin_cap;
   r.heavy_on = o.heavy_detection >= 0 ? 1 : 0;
+  r.merge_generic = o.merge == DTSORT_MERGE_GENERIC ? 1 : 0;
   r.sample_factor = o.sample_log_factor > 0 ? o.sample_log_factor : 1;
   r.seed = o.seed ? o.seed : 1;
   r.debug_fault = o.debug_fault;
@@ -378,6 +379,7 @@ dtsort_status run_sort(dtsort_handle h, int op, void *keys, void *vals, const in
   P.gamma_max = std::min(o.gamma_max, dts::GAMMA_HW);
   P.cap = L.cap;
   P.heavy_on = o.heavy_on;
+  P.merge_generic = o.merge_generic;
   P.target = L.target;
   P.seed = o.seed;
   P.sample_factor = o.sample_factor;
@@ -577,7 +579,8 @@ dtsort_status dtsort_set_options(dtsort_handle h, const dtsort_options *opt) {
        opt->bucketing != DTSORT_BUCKETING_LEARNED_ALWAYS) ||
       opt->learned_segments < 0 || opt->learned_train_steps < 0 || opt->wait_limit_ms < 0 ||
       opt->debug_fault < 0 || opt->debug_fault > 1 || opt->launch_mode < 0 ||
-      opt->launch_mode > 2 || opt->block_tiles < 0 || opt->block_tiles > 8)
+      opt->launch_mode > 2 || opt->block_tiles < 0 || opt->block_tiles > 8 ||
+      (opt->merge != DTSORT_MERGE_DOVETAIL && opt->merge != DTSORT_MERGE_GENERIC))
     return DTSORT_ERR_INVALID_ARG;
   h->opt = *opt;
   return DTSORT_OK;

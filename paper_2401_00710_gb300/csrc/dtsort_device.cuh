@@ -39,6 +39,7 @@ constexpr int HASH_HW = 1 << GAMMA_HW;        // hash slots: 4 per heavy key (<=
 constexpr int MAXLEV = 136;                   // > 2 * 64 + slack
 constexpr int64_t COPY_CHUNK = 1 << 16;       // records per plain-copy task
 constexpr int MERGE_CHUNK = 8192;             // output records per merge item
+constexpr int MERGE_SUB = 2048;               // generic merge: outputs staged at a time
 constexpr int FIN_DIG = 8;                    // base-case digit bits
 constexpr int FIN_NB = (1 << FIN_DIG) + 8;    // 256 digits + dummy, padded
 constexpr int FIN_IB = 13;                    // index bits of a base-case composite
@@ -156,6 +157,7 @@ struct Params {
   int32_t gamma_max;
   int32_t cap;            // largest base-case bucket
   int32_t heavy_on;
+  int32_t merge_generic;  // 1: merge-path merge of each zone instead of Alg. 3
   int64_t target;         // desired bucket size after distribution
   uint64_t seed;
   int32_t sample_factor;  // samples = 2^gamma * L * factor (capped)

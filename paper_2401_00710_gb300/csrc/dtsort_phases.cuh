@@ -122,8 +122,14 @@ constexpr size_t phase_smem_bytes(int ph) {
     case 0:                                    // KP_SEED
     case 1: return 8 * (NWARP + 1) + 256;      // KP_SETUP
     case 9:                                    // KP_MERGE_PREP
-    case 10:                                   // KP_MERGE: heavy runs, warp sums
-      return 3 * (16 + 8 * (HASH_HW / 2 + 1)) + 16 + 8 * (NWARP + 1) + 16 + sizeof(MZone) + 256;
+    case 10: {                                 // KP_MERGE: heavy runs, warp sums;
+      const size_t dov =                       // or the generic merge's sub-tile
+          3 * (16 + 8 * (HASH_HW / 2 + 1)) + 16 + 8 * (NWARP + 1) + 16 + sizeof(MZone) + 256;
+      const size_t gen = 16 + sizeof(K) * MERGE_SUB + 16 + sizeof(K) * (HV ? MERGE_SUB : 1) +
+                         16 + 2 * MERGE_SUB + 16 + 8 * (MERGE_CHUNK / MERGE_SUB + 1) + 16 +
+                         sizeof(MZone) + 256;
+      return dov > gen ? dov : gen;
+    }
     case 11: return 256;                       // KP_STATS
     default: return smem_bytes<K, HV>();       // scatter, base case
   }
@@ -1599,6 +1605,7 @@ __device__ void phase_finish(const Params &P, int level, unsigned char *smem) {
 // Alg. 3); every other position takes the next light record.
 template <typename K, bool HV>
 __device__ void phase_merge_prep(const Params &P, int level, unsigned char *smem) {
+  if (P.merge_generic) return;  // the generic merge needs no heavy-run starts
   Ctl *c = P.ctl;
   const int64_t z0 = min(ld_cg64(&c->lvl_zone[level]), (long long)P.mhmax);
   const int64_t z1 = min(ld_cg64(&c->lvl_zone[level + 1]), (long long)P.mhmax);
@@ -1630,8 +1637,145 @@ __device__ void phase_merge_prep(const Params &P, int level, unsigned char *smem
   }
 }
 
+// Generic merging, the comparison for Alg. 3: in each zone the sorted light
+// bucket A = [zs, zs + b0) and the concatenation B = [zs + b0, ze) of the
+// heavy buckets (sorted: they are numbered by key) are merged stably by merge
+// path, A first on equal keys, with key comparisons only.  A work item of
+// MERGE_CHUNK outputs is cut into sub-tiles of MERGE_SUB; the split of every
+// sub-tile boundary d (how many of the zone's first d outputs come from A) is
+// found by one warp with a 32-ary search; each sub-tile's inputs are staged in
+// shared memory, every thread merges MERGE_SUB / NT outputs after a merge-path
+// search of its own, and the sub-tile is written out in order.
+
+// First i in [max(0, d - nb), min(d, na)] with B[d - 1 - i] < A[i] (the upper
+// end when none): a warp probes 32 evenly spaced candidates per round (the
+// predicate is monotone in i).  Every lane returns the split.
+template <typename K>
+__device__ __forceinline__ int64_t merge_split_warp(const K *A, int64_t na, const K *B,
+                                                    int64_t nb, int64_t d, int lane) {
+  int64_t lo = d > nb ? d - nb : 0, hi = d < na ? d : na;
+  while (lo < hi) {
+    const int64_t step = (hi - lo + 31) / 32;
+    const int64_t p = lo + (int64_t)lane * step;
+    bool before = false;  // A[p] is among the first d outputs
+    if (p < hi) before = !(ld_key<K>(B + (d - 1 - p)) < ld_key<K>(A + p));
+    const int cnt = __popc(__ballot_sync(0xffffffffu, before));  // lanes 0..cnt-1
+    const int64_t nlo = cnt > 0 ? lo + (int64_t)(cnt - 1) * step + 1 : lo;
+    const int64_t pc = lo + (int64_t)cnt * step;
+    hi = (cnt < 32 && pc < hi) ? pc : hi;
+    lo = nlo;
+  }
+  return lo;
+}
+
+template <typename K, bool HV>
+__device__ void phase_merge_generic(const Params &P, int level) {
+  constexpr int E = MERGE_SUB / NT;
+  constexpr int NSUB = MERGE_CHUNK / MERGE_SUB;
+  static_assert(E * NT == MERGE_SUB && NSUB * MERGE_SUB == MERGE_CHUNK && NSUB < NWARP,
+                "one warp per sub-tile boundary");
+  static_assert(MERGE_SUB <= 65536, "16-bit source indices");
+  Ctl *c = P.ctl;
+  const int64_t z0 = min(ld_cg64(&c->lvl_zone[level]), (long long)P.mhmax);
+  const int64_t z1 = min(ld_cg64(&c->lvl_zone[level + 1]), (long long)P.mhmax);
+  const int64_t c0 = (int64_t)__ldcg(&c->lvl_chunk[level]);
+  const int64_t c1 = (int64_t)__ldcg(&c->lvl_chunk[level + 1]);
+  Carve cv;
+  K *sk = cv.take<K>(MERGE_SUB);
+  K *sv = cv.take<K>(HV ? MERGE_SUB : 1);
+  uint16_t *sidx = cv.take<uint16_t>(MERGE_SUB);
+  long long *spl = cv.take<long long>(NSUB + 1);
+  MZone *Zs = cv.take<MZone>(1);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  long long my = 0;
+  int64_t curz = -1;
+  for (int64_t ch = c0 + blockIdx.x; ch < c1; ch += gridDim.x) {
+    int64_t a = z0, b = z1 - 1;
+    while (a < b) {
+      const int64_t mid = (a + b + 1) >> 1;
+      if (__ldcg((const long long *)&P.zones[mid].chunk0) <= ch) a = mid;
+      else b = mid - 1;
+    }
+    if (a != curz) {
+      __syncthreads();
+      if (threadIdx.x == 0) *Zs = ldcg_obj(&P.zones[a]);
+      __syncthreads();
+      curz = a;
+    }
+    const MZone Z = *Zs;
+    const int64_t na = Z.b0, nb = Z.ze - Z.zs - Z.b0;
+    const int64_t o0 = Z.zs + (ch - Z.chunk0) * MERGE_CHUNK;
+    const int64_t o1 = o0 + MERGE_CHUNK < Z.ze ? o0 + MERGE_CHUNK : Z.ze;
+    if (Z.obuf > 1 || na < 0 || nb < 0 || ch < Z.chunk0 || o0 >= o1) {
+      if (threadIdx.x == 0) latch(P, ERR_INTERNAL);
+      __syncthreads();
+      continue;
+    }
+    const int ib = Z.obuf ^ 1;
+    const K *kin = (const K *)P.keys[ib];
+    K *kout = (K *)P.keys[Z.obuf];
+    const K *vin = HV ? (const K *)P.vals[ib] : nullptr;
+    K *vout = HV ? (K *)P.vals[Z.obuf] : nullptr;
+    const int ns = (int)((o1 - o0 + MERGE_SUB - 1) / MERGE_SUB);
+    if (w <= ns) {
+      const int64_t e = o0 + (int64_t)w * MERGE_SUB < o1 ? o0 + (int64_t)w * MERGE_SUB : o1;
+      const int64_t sp = merge_split_warp<K>(kin + Z.zs, na, kin + Z.zs + Z.b0, nb, e - Z.zs, lane);
+      if (lane == 0) spl[w] = sp;
+    }
+    __syncthreads();
+    for (int s = 0; s < ns; ++s) {
+      const int64_t sb = o0 + (int64_t)s * MERGE_SUB;
+      const int64_t se = sb + MERGE_SUB < o1 ? sb + MERGE_SUB : o1;
+      const int64_t i0 = spl[s], i1 = spl[s + 1];
+      const int64_t j0 = (sb - Z.zs) - i0, j1 = (se - Z.zs) - i1;
+      const int n2 = (int)(se - sb);
+      if (i0 < 0 || i1 < i0 || i1 > na || j0 < 0 || j1 < j0 || j1 > nb) {
+        if (threadIdx.x == 0) latch(P, ERR_INTERNAL);
+        break;  // block-uniform: the splits are in shared memory
+      }
+      const int la = (int)(i1 - i0), lb = (int)(j1 - j0);  // la + lb = n2
+      for (int q = threadIdx.x; q < n2; q += NT) {
+        const int64_t g = q < la ? Z.zs + i0 + q : Z.zs + Z.b0 + j0 + (q - la);
+        sk[q] = ld_key<K>(kin + g);
+        if constexpr (HV) sv[q] = ld_key<K>(vin + g);
+      }
+      __syncthreads();
+      const int d = threadIdx.x * E;
+      if (d < n2) {
+        int lo = d > lb ? d - lb : 0, hi = d < la ? d : la;
+        while (lo < hi) {
+          const int mid = (lo + hi) >> 1;
+          if (!(sk[la + d - 1 - mid] < sk[mid])) lo = mid + 1;
+          else hi = mid;
+        }
+        int ia = lo, jb = d - lo;
+#pragma unroll
+        for (int r = 0; r < E; ++r) {
+          if (d + r < n2) {
+            const bool fromA = ia < la && (jb >= lb || !(sk[la + jb] < sk[ia]));
+            sidx[d + r] = (uint16_t)(fromA ? ia++ : la + jb++);
+          }
+        }
+      }
+      __syncthreads();
+      for (int q = threadIdx.x; q < n2; q += NT) {
+        const int x = sidx[q];
+        kout[sb + q] = sk[x];
+        if constexpr (HV) vout[sb + q] = sv[x];
+      }
+      __syncthreads();
+    }
+    my += o1 - o0;
+  }
+  if (threadIdx.x == 0 && my) atomic_add_ll(&c->st_merge_records, my);
+}
+
 template <typename K, bool HV>
 __device__ void phase_merge(const Params &P, int level, unsigned char *smem) {
+  if (P.merge_generic) {
+    phase_merge_generic<K, HV>(P, level);
+    return;
+  }
   Ctl *c = P.ctl;
   const int64_t z0 = min(ld_cg64(&c->lvl_zone[level]), (long long)P.mhmax);
   const int64_t z1 = min(ld_cg64(&c->lvl_zone[level + 1]), (long long)P.mhmax);

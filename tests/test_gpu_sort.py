@@ -223,6 +223,31 @@ def test_options_do_not_change_output(G, opts):
         check(G, keys, vals)
 
 
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_generic_merge_matches(G, mode):
+    # the merge ablation: merge-path merging of every heavy zone (key
+    # comparisons) instead of dovetail merging gives the same stable order
+    zones = {}
+    for name, dtype, n, seed in (("zipf1.2", np.uint32, 3_000_000, 1),
+                                 ("distinct10", np.uint32, 1_300_007, 16),
+                                 ("exp", np.uint32, 1_300_007, 16),
+                                 ("heavymix", np.uint64, 1_300_007, 16),
+                                 ("zipf1.2hash", np.uint64, 1_300_007, 16)):
+        keys = gen.family(name, n, dtype, seed=seed)
+        vals = gen.iota(n, dtype)
+        G.set_options(merge=dts.DTSORT_MERGE_GENERIC, launch_mode=mode)
+        st = check(G, keys, vals)
+        zones[name] = (st["merge_zones"], st["merge_records"])
+        check(G, keys, None)
+    assert zones["zipf1.2"][0] > 0 and zones["zipf1.2"][1] > 0, zones
+    G.reset_options()
+    o = dts.dtsort_default_options()
+    o.merge = 2
+    with pytest.raises(dts.DtsortError) as e:
+        dts.dtsort_set_options(G.h, o)
+    assert e.value.status == dts.DTSORT_ERR_INVALID_ARG
+
+
 @pytest.mark.parametrize("mode", [1, 2])
 def test_launch_modes_match(G, mode):
     # 1: one launch per phase, host-driven (profiling aid); 2: the persistent
