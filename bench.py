@@ -326,10 +326,26 @@ def run_ours(args):
                        "learned": dts.DTSORT_BUCKETING_LEARNED,
                        "learned-always": dts.DTSORT_BUCKETING_LEARNED_ALWAYS}[args.bucketing]
         dts.dtsort_set_options(h, o)
-    wsb = dts.dtsort_workspace_bytes(h, op, n)
-    ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
     sp = stream.cuda_stream
+    tuned = None
+    if args.autotune:
+        # time the autotuner's candidates on this input, then sort with its
+        # cached choice
+        o_ = dts.dtsort_get_options(h)
+        o_.autotune = 1
+        dts.dtsort_set_options(h, o_)
+        sb = dts.dtsort_autotune_scratch_bytes(h, op, n, 1)
+        scratch = torch.empty(sb, dtype=torch.uint8, device=dev)
+        st, best = dts.dtsort_autotune(h, op, pk.data_ptr(), pv.data_ptr() if has_v else None,
+                                       None, 0, n, scratch.data_ptr(), sb, sp)
+        if st != 0:
+            raise RuntimeError(dts.status_string(st))
+        tuned = {"gamma_max": best.gamma_max, "finisher_capacity": best.finisher_capacity,
+                 "block_tiles": best.block_tiles}
+        del scratch
+    wsb = dts.dtsort_workspace_bytes(h, op, n)
+    ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
     fn = {dts.DTSORT_OP_U32_KV: dts.dtsort_u32_kv, dts.DTSORT_OP_U64_KV: dts.dtsort_u64_kv,
           dts.DTSORT_OP_U32: dts.dtsort_u32, dts.DTSORT_OP_U64: dts.dtsort_u64}[op]
 
@@ -426,7 +442,7 @@ def run_ours(args):
                                   ", heavy-key detection off" if args.heavy == "off" else "",
                                   ", generic merge-path merging" if args.merge == "generic"
                                   else ""),
-                   "n": n, "dist": args.dist,
+                   "n": n, "dist": args.dist, "autotuned": tuned,
                    "l2": ("inputs %.1f GB per step >> L2 (129 MB)" % (rec_bytes * n / 1e9)
                           if rec_bytes * n > 4 * 129e6 else
                           "inputs %.0f MB per step: not much larger than L2 (129 MB)"

@@ -261,9 +261,13 @@ __device__ __forceinline__ int levels_below(double s, double cap, double target,
 // Whether learned level-0 zones pay, from the sorted model sample (m keys of
 // the n): the record-passes below level 0 with the digit zones against those
 // with the model's zones [spl[z], spl[z+1]) plus the learned level's extra
-// cost of `penalty` record-passes per record; each zone's size is estimated
-// from the sample and costs the levels it needs.  One CTA; writes the
-// decision and both estimates (per record).
+// cost of `penalty` record-passes per record.  Each zone's cost follows the
+// digit levels below it along the child that holds the median of its sample
+// keys (a skewed zone splits off only its top key bits per level, so its bulk
+// passes through many levels): every subproblem on that path above the
+// base-case capacity is distributed once, and the other children of each
+// step cost the levels the digit-width rule gives their mean size.  One CTA,
+// a thread per zone; writes the decision and both estimates (per record).
 template <typename K>
 __global__ void __launch_bounds__(512) lrn_decide_kernel(
     const uint64_t *__restrict__ sorted, int64_t m, int64_t n, int key_bits, int B,
@@ -276,8 +280,8 @@ __global__ void __launch_bounds__(512) lrn_decide_kernel(
   const int g = 31 - __clz(B);
   const int lo = t - g > 0 ? t - g : 0;
   const int nz = 1 << (t - lo);
-  auto lower_bound = [&](uint64_t v) -> int64_t {  // first index with sorted[i] >= v
-    int64_t a = 0, b = m;
+  // first index in [a, b) with sorted[i] >= v (b when none)
+  auto lower_bound_in = [&](int64_t a, int64_t b, uint64_t v) -> int64_t {
     while (a < b) {
       const int64_t mid = (a + b) >> 1;
       if (sorted[mid] < v) a = mid + 1;
@@ -285,9 +289,41 @@ __global__ void __launch_bounds__(512) lrn_decide_kernel(
     }
     return a;
   };
+  auto lower_bound = [&](uint64_t v) -> int64_t { return lower_bound_in(0, m, v); };
+  const double per = (double)n / (double)m;  // records per sample key
   auto cost = [&](int64_t c0, int64_t c1) {
-    const double s = (double)(c1 - c0) * (double)n / (double)m;
-    return s * (double)levels_below(s, (double)cap, (double)target, gmax);
+    double total = 0.0;
+    int64_t a = c0, b = c1;
+    for (int step = 0; step < 64 && b > a; ++step) {
+      const double s = (double)(b - a) * per;
+      if (s <= (double)cap) break;
+      const uint64_t kmin = sorted[a] & mask, kmax = sorted[b - 1] & mask;
+      if (kmin == kmax) break;  // one key value: moved, not distributed
+      total += s;               // this subproblem is distributed once
+      // its digit: the width rule's bits at the top of its key range
+      int e = 0;
+      while (e < 62 && (double)target * (double)(1ull << e) < s) ++e;
+      if (e < 1) e = 1;
+      const int nlev = (e + gmax - 1) / gmax;
+      int gw = (e + nlev - 1) / nlev;
+      gw = gw > gmax ? gmax : gw;
+      const int t = 64 - __clzll((long long)(kmax - kmin));
+      gw = gw > t ? t : gw;
+      const int sh = t - gw;
+      const uint64_t d = ((sorted[a + (b - a) / 2] & mask) - kmin) >> sh;
+      const uint64_t lo_v = kmin + (d << sh);
+      const uint64_t hi_v = sh < 64 ? lo_v + (1ull << sh) : lo_v;
+      const int64_t na = lower_bound_in(a, b, lo_v);
+      const int64_t nb = hi_v > lo_v ? lower_bound_in(na, b, hi_v) : b;
+      // the other children at their mean size
+      const double so = (double)((b - a) - (nb - na)) * per;
+      const double mean = so / (double)((1ull << gw) - 1ull);
+      total += so * (double)levels_below(mean, (double)cap, (double)target, gmax);
+      if (nb - na >= b - a) break;  // no progress (cannot happen: kmin < kmax)
+      a = na;
+      b = nb;
+    }
+    return total;
   };
   double ad = 0.0, al = 0.0;
   for (int z = threadIdx.x; z < nz; z += blockDim.x)
