@@ -59,3 +59,33 @@ def test_product_path_fails_loudly_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(dts, "_lib", None)
     with pytest.raises(RuntimeError):
         dts.lib()
+
+
+@pytest.mark.parametrize("cls,cname", [(dts.dtsort_options, "dtsort_options"),
+                                       (dts.dtsort_stats, "dtsort_stats")])
+def test_binding_structs_match_the_header(cls, cname, tmp_path):
+    # the ctypes mirrors of the header's structs: every field at the C
+    # compiler's offset, and the same total size (a field added to or dropped
+    # from one side only would shift the ones after it)
+    import ctypes
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "dtsort.h"',
+             "int main(void) {",
+             '  printf("size %%zu\\n", sizeof(%s));' % cname]
+    for name, _ in cls._fields_:
+        lines.append('  printf("%s %%zu\\n", offsetof(%s, %s));' % (name, cname, name))
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c99", "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)],
+                   check=True, capture_output=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout
+    got = dict(line.split() for line in out.strip().splitlines())
+    assert int(got["size"]) == ctypes.sizeof(cls)
+    for name, _ in cls._fields_:
+        assert int(got[name]) == getattr(cls, name).offset, name
