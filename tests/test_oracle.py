@@ -341,6 +341,30 @@ def test_bucket_ids_hand_example_r16_gamma2():
     assert nb == 7
 
 
+def _golden(name):
+    """A text fixture under tests/golden: '#' comments, then 'field v1 v2 ...'
+    lines; returns {field: [int, ...]}."""
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", name)
+    out = {}
+    for line in open(path):
+        line = line.split("#", 1)[0].split()
+        if line:
+            out[line[0]] = [int(v) for v in line[1:]]
+    return out
+
+
+def test_golden_overflow_bucket_example():
+    # the paper's overflow-bucket example (see the fixture's header): two key
+    # bits, largest sampled key 1 -> zones 00 and 01, keys 10 and 11 overflow
+    g = _golden("overflow_bucket_two_bits.txt")
+    keys = np.array(g["keys"], dtype=W32)
+    for gamma in g["gamma"]:
+        assert oracle.zone_layout(g["sample_max"][0], g["hi"][0], gamma) == tuple(g["zone_bits"])
+        ids, nb = oracle.bucket_ids([], g["sample_max"][0], g["hi"][0], gamma, keys)
+        np.testing.assert_array_equal(ids, g["ids"])
+        assert nb == g["buckets"][0]
+
+
 def test_zone_layout():
     assert oracle.zone_layout(15, 4, 2) == (4, 2)
     assert oracle.zone_layout(7, 4, 2) == (3, 1)
@@ -449,6 +473,7 @@ def _run_pins():
     test_stable_positions_match_definition()
     test_heavy_rule_hand_example()
     test_bucket_ids_hand_example_r16_gamma2()
+    test_golden_overflow_bucket_example()
     test_dtmerge_equals_stable_sort(3)
     test_dtmerge_equals_stable_sort(400)
 
@@ -470,6 +495,21 @@ def test_planted_mistakes_are_caught(mutant, tmp_path):
     with oracle.using_library(str(so)):
         with pytest.raises(AssertionError):
             _run_pins()
+
+
+def test_golden_example_catches_the_overflow_mistake(tmp_path):
+    # the paper's overflow example alone fails on the oracle built with its
+    # overflow test off by one bit
+    src = open(ORACLE_SRC).read()
+    old, new = MUTANTS["overflow_bit"]
+    mpath = tmp_path / "mutant.c"
+    mpath.write_text(src.replace(old, new))
+    so = tmp_path / "libmutant.so"
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC",
+                           "-pthread", str(mpath), "-o", str(so)])
+    with oracle.using_library(str(so)):
+        with pytest.raises(AssertionError):
+            test_golden_overflow_bucket_example()
 
 
 # ------------------------------------------------ check of a claimed output
