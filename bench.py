@@ -235,6 +235,26 @@ def cpu_oracle_time(args, sample):
     return sample / dt, cores, dt
 
 
+def single_config(args, world, tuned=None):
+    """The `config` of a single-array sort line; both arms print the same."""
+    rec_bytes = np.dtype(key_dtype(args.op)).itemsize * (2 if args.op.endswith("kv") else 1)
+    n = args.n
+    return {"workload": "stable sort, %s, n=%d, keys %s seed %d, values = %s%s%s%s"
+                        % (args.op, n, args.dist, args.seed,
+                           "the edges' sources (graph transpose of a power-law "
+                           "edge list over 2^26 vertices)" if args.dist == "edges"
+                           else "index",
+                           "" if args.bucketing == "digit" else ", bucketing " + args.bucketing,
+                           ", heavy-key detection off" if args.heavy == "off" else "",
+                           ", generic merge-path merging" if args.merge == "generic" else ""),
+            "n": n, "dist": args.dist, "autotuned": tuned,
+            "l2": ("inputs %.1f GB per step >> L2 (129 MB)" % (rec_bytes * n / 1e9)
+                   if rec_bytes * n > 4 * 129e6 else
+                   "inputs %.0f MB per step: not much larger than L2 (129 MB)"
+                   % (rec_bytes * n / 1e6)),
+            "parallelism": "replicas" if world > 1 else "single"}
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -253,9 +273,7 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": args.op, "data": "synthetic",
-            "config": {"workload": "%s %s n=%d (oracle on a %d-record sample of the same "
-                                   "stream)" % (args.op, args.dist, args.n, sample),
-                       "n": args.n, "dist": args.dist},
+            "config": single_config(args, world),
             "impl": "reference",
             "cpu_baseline": {"value": value, "unit": "keys/s", "cores": cores,
                              "kind": "oracle",
@@ -268,6 +286,8 @@ def run_reference(args):
 
 def device_error_text(h, st):
     """Status text plus the first failed internal check, if one was recorded."""
+    import paper_2401_00710_gb300 as dts
+
     text = dts.status_string(st)
     if st == dts.DTSORT_ERR_INTERNAL:
         try:
@@ -424,7 +444,6 @@ def run_ours(args):
     if rank != 0:
         return 0
     peak, peak_kind = peaks()
-    rec_bytes = kbytes * (2 if has_v else 1)
     b_alg = B_ALG[args.op] * n
     achieved = b_alg / (ms_step / 1e3) / 1e9
     line = {
@@ -432,22 +451,7 @@ def run_ours(args):
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": args.op, "data": "synthetic",
-        "config": {"workload": "stable sort, %s, n=%d, keys %s seed %d, values = %s%s%s%s"
-                               % (args.op, n, args.dist, args.seed,
-                                  "the edges' sources (graph transpose of a power-law "
-                                  "edge list over 2^26 vertices)" if args.dist == "edges"
-                                  else "index",
-                                  "" if args.bucketing == "digit"
-                                  else ", bucketing " + args.bucketing,
-                                  ", heavy-key detection off" if args.heavy == "off" else "",
-                                  ", generic merge-path merging" if args.merge == "generic"
-                                  else ""),
-                   "n": n, "dist": args.dist, "autotuned": tuned,
-                   "l2": ("inputs %.1f GB per step >> L2 (129 MB)" % (rec_bytes * n / 1e9)
-                          if rec_bytes * n > 4 * 129e6 else
-                          "inputs %.0f MB per step: not much larger than L2 (129 MB)"
-                          % (rec_bytes * n / 1e6)),
-                   "parallelism": "replicas" if world > 1 else "single"},
+        "config": single_config(args, world, tuned),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak,
                      "traffic": dram_traffic(args.op, args.dist, n)
