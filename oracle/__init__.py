@@ -12,6 +12,8 @@ module only marshals numpy arrays.  What each function follows:
   records reordered into non-decreasing key order, stably.  The unique answer
   is the lexicographic order of (key, original index).
 * ``stable_positions`` -- the same definition for single records.
+* ``check_sorted_keys`` -- the same definition for key-only output, where
+  stability is unobservable: the input's multiset in non-decreasing order.
 * ``splitmix64_*`` -- SplitMix64 (Steele, Lea, Flood 2014), the sampler's draws.
 * ``sample_positions`` / ``heavy_from_sample`` / ``sample_heavy`` -- Alg. 2
   step 1 (Sec. 3.1): sample, sort, subsample every (log n)-th key, keys seen
@@ -92,6 +94,8 @@ def _declare(L):
     L.oracle_stable_positions.restype = _INT
     L.oracle_check_stable.argtypes = [_P, _P, _P, _INT, _INT, _I64, _INT]
     L.oracle_check_stable.restype = _I64
+    L.oracle_check_sorted_keys.argtypes = [_P, _P, _INT, _I64, _INT]
+    L.oracle_check_sorted_keys.restype = _I64
     L.oracle_splitmix64_next.argtypes = [ctypes.POINTER(_U64)]
     L.oracle_splitmix64_next.restype = _U64
     L.oracle_splitmix64_at.argtypes = [_U64, _U64]
@@ -175,6 +179,19 @@ def check_stable(keys_in, keys_out, idx_out, nthreads=0):
     return int(lib().oracle_check_stable(_ptr(keys_in), _ptr(keys_out), _ptr(idx_out),
                                          _kbytes(keys_in), idx_out.dtype.itemsize,
                                          len(keys_in), nthreads))
+
+
+def check_sorted_keys(keys_in, keys_out, nthreads=0):
+    """-1 if keys_out is the key-only sort of keys_in (the input's multiset of
+    keys in non-decreasing order), else the first failing output slot."""
+    keys_in = np.ascontiguousarray(keys_in)
+    keys_out = np.ascontiguousarray(keys_out)
+    assert keys_in.dtype == keys_out.dtype and len(keys_in) == len(keys_out)
+    r = int(lib().oracle_check_sorted_keys(_ptr(keys_in), _ptr(keys_out), _kbytes(keys_in),
+                                           len(keys_in), nthreads))
+    if r == -2:
+        raise MemoryError("oracle_check_sorted_keys: out of memory")
+    return r
 
 
 def stable_positions(keys, js, nthreads=0):

@@ -20,6 +20,11 @@
  *                            index) must be strictly increasing, the indices a
  *                            permutation of 0..n-1, and each key the input key
  *                            at its index; exactly one output passes.
+ *   oracle_check_sorted_keys The definition for key-only output, where
+ *                            stability is unobservable: the input's multiset
+ *                            of keys in non-decreasing order (order of
+ *                            adjacent slots, and every key value as often as
+ *                            in the input, counted per top-16-bit group).
  *   oracle_splitmix64_*      The SplitMix64 generator (Steele, Lea, Flood,
  *                            OOPSLA 2014), used for the sampler's random draws.
  *   oracle_sample_*          Alg. 2 step 1 (Sec. 3.1): draw the sample S, sort
@@ -347,6 +352,180 @@ int64_t oracle_check_stable(const void *kin, const void *kout, const void *idx, 
       if (!seen[i]) { first = n; break; }
   free(seen); free(jobs); free(th);
   return first;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Check of a claimed key-only sorted output (Sec. 2.3 definition).          */
+/* ------------------------------------------------------------------------ */
+/* Without values stability cannot be observed: the unique answer is the
+ * input's multiset of keys in non-decreasing order.  The check reads that
+ * definition directly: (1) the output is non-decreasing; (2) it holds every
+ * key value exactly as often as the input does.  (2) is counted per group of
+ * keys sharing their top 16 bits: the group's input count must equal its
+ * output count (the output being sorted, each group is then one contiguous
+ * range of it), and inside a group every distinct output key, read as a run
+ * of equal keys, must receive from the input exactly as many keys as the run
+ * is long, with no input key left without a run. */
+
+#define CSK_BITS 16
+#define CSK_G ((int64_t)1 << CSK_BITS)
+
+static uint64_t csk_group(uint64_t k, int kbytes) { return k >> (8 * kbytes - CSK_BITS); }
+
+typedef struct {
+  const void *kin, *kout;
+  int kbytes;
+  int64_t n, lo, hi;
+  int64_t *cin, *cout;   /* this thread's group counts */
+  int64_t bad;           /* first unsorted output slot + 1, or 0 */
+} csk_count_t;
+
+static void *csk_count_main(void *arg) {
+  csk_count_t *j = (csk_count_t *)arg;
+  for (int64_t i = j->lo; i < j->hi; ++i) {
+    const uint64_t a = key_at(j->kout, j->kbytes, i);
+    if (!j->bad && i + 1 < j->n && a > key_at(j->kout, j->kbytes, i + 1)) j->bad = i + 1;
+    j->cout[csk_group(a, j->kbytes)] += 1;
+    j->cin[csk_group(key_at(j->kin, j->kbytes, i), j->kbytes)] += 1;
+  }
+  return NULL;
+}
+
+typedef struct {
+  const void *kin;
+  int kbytes;
+  int64_t lo, hi;
+  int64_t *pos;          /* this thread's next slot per group */
+  uint64_t *grouped;     /* input keys, grouped */
+} csk_scatter_t;
+
+static void *csk_scatter_main(void *arg) {
+  csk_scatter_t *j = (csk_scatter_t *)arg;
+  for (int64_t i = j->lo; i < j->hi; ++i) {
+    const uint64_t k = key_at(j->kin, j->kbytes, i);
+    j->grouped[j->pos[csk_group(k, j->kbytes)]++] = k;
+  }
+  return NULL;
+}
+
+typedef struct {
+  const void *kout;
+  int kbytes;
+  const int64_t *start;  /* group g: output and grouped input [start[g], start[g+1]) */
+  const uint64_t *grouped;
+  int64_t *next;         /* shared group counter */
+  int64_t bad;           /* first slot of a mismatching group + 1, or 0; -1 no memory */
+} csk_match_t;
+
+/* runs of the sorted output range: distinct keys and their lengths */
+static int64_t csk_runs(const void *kout, int kbytes, int64_t a, int64_t b, uint64_t *rk,
+                        int64_t *rlen) {
+  int64_t r = 0;
+  for (int64_t i = a; i < b; ++i) {
+    const uint64_t k = key_at(kout, kbytes, i);
+    if (r == 0 || rk[r - 1] != k) { rk[r] = k; rlen[r] = 0; ++r; }
+    rlen[r - 1] += 1;
+  }
+  return r;
+}
+
+static void *csk_match_main(void *arg) {
+  csk_match_t *j = (csk_match_t *)arg;
+  while (1) {
+    const int64_t g = __atomic_fetch_add(j->next, 1, __ATOMIC_RELAXED);
+    if (g >= CSK_G) break;
+    const int64_t a = j->start[g], b = j->start[g + 1];
+    if (b == a) continue;
+    uint64_t *rk = (uint64_t *)malloc((size_t)(b - a) * sizeof(uint64_t));
+    int64_t *rlen = (int64_t *)malloc((size_t)(b - a) * sizeof(int64_t));
+    if (!rk || !rlen) { free(rk); free(rlen); j->bad = -1; return NULL; }
+    const int64_t r = csk_runs(j->kout, j->kbytes, a, b, rk, rlen);
+    int ok = 1;
+    for (int64_t i = a; i < b && ok; ++i) {
+      const uint64_t k = j->grouped[i];
+      int64_t lo = 0, hi = r;  /* first run whose key is >= k */
+      while (lo < hi) {
+        const int64_t mid = lo + (hi - lo) / 2;
+        if (rk[mid] < k) lo = mid + 1; else hi = mid;
+      }
+      if (lo == r || rk[lo] != k || rlen[lo] == 0) ok = 0;  /* no run left for k */
+      else rlen[lo] -= 1;
+    }
+    /* equal totals and no key without a run: every run was used up exactly */
+    free(rk); free(rlen);
+    if (!ok && (j->bad == 0 || a + 1 < j->bad)) j->bad = a + 1;
+  }
+  return NULL;
+}
+
+/* Returns -1 if kout[0..n) is the input's multiset of keys in non-decreasing
+ * order; else the first output slot that is out of order, or the first slot
+ * of a group of keys whose multiset differs; -2 if memory ran out. */
+int64_t oracle_check_sorted_keys(const void *kin, const void *kout, int kbytes, int64_t n,
+                                 int nthreads) {
+  if (n <= 0) return -1;
+  if (nthreads <= 0) nthreads = oracle_default_threads();
+  if ((int64_t)nthreads > n) nthreads = (int)n;
+  const int T = nthreads;
+  int64_t *cnt = (int64_t *)calloc((size_t)T * 2 * CSK_G, sizeof(int64_t));
+  int64_t *start = (int64_t *)malloc((size_t)(CSK_G + 1) * sizeof(int64_t));
+  uint64_t *grouped = (uint64_t *)malloc((size_t)n * sizeof(uint64_t));
+  csk_count_t *cj = (csk_count_t *)calloc((size_t)T, sizeof(csk_count_t));
+  csk_scatter_t *sj = (csk_scatter_t *)calloc((size_t)T, sizeof(csk_scatter_t));
+  csk_match_t *mj = (csk_match_t *)calloc((size_t)T, sizeof(csk_match_t));
+  pthread_t *th = (pthread_t *)calloc((size_t)T, sizeof(pthread_t));
+  int64_t result = -1;
+  if (!cnt || !start || !grouped || !cj || !sj || !mj || !th) { result = -2; goto done; }
+  /* (1) order, and the group counts of both sides */
+  for (int t = 0; t < T; ++t) {
+    cj[t].kin = kin; cj[t].kout = kout; cj[t].kbytes = kbytes; cj[t].n = n;
+    cj[t].lo = n * t / T; cj[t].hi = n * (t + 1) / T;
+    cj[t].cin = cnt + (size_t)t * 2 * CSK_G;
+    cj[t].cout = cj[t].cin + CSK_G;
+    pthread_create(&th[t], NULL, csk_count_main, &cj[t]);
+  }
+  for (int t = 0; t < T; ++t) pthread_join(th[t], NULL);
+  for (int t = 0; t < T; ++t)
+    if (cj[t].bad) { result = cj[t].bad - 1; goto done; }
+  /* (2a) equal group counts; group g is output range [start[g], start[g+1]) */
+  start[0] = 0;
+  for (int64_t g = 0; g < CSK_G; ++g) {
+    int64_t ci = 0, co = 0;
+    for (int t = 0; t < T; ++t) { ci += cj[t].cin[g]; co += cj[t].cout[g]; }
+    if (ci != co) { result = start[g]; goto done; }
+    start[g + 1] = start[g] + ci;
+  }
+  /* (2b) the input keys grouped the same way (each thread its own slots) */
+  for (int64_t g = 0; g < CSK_G; ++g) {
+    int64_t p = start[g];
+    for (int t = 0; t < T; ++t) {
+      const int64_t c = cj[t].cin[g];
+      cj[t].cin[g] = p;  /* becomes thread t's next slot in group g */
+      p += c;
+    }
+  }
+  for (int t = 0; t < T; ++t) {
+    sj[t].kin = kin; sj[t].kbytes = kbytes;
+    sj[t].lo = n * t / T; sj[t].hi = n * (t + 1) / T;
+    sj[t].pos = cj[t].cin; sj[t].grouped = grouped;
+    pthread_create(&th[t], NULL, csk_scatter_main, &sj[t]);
+  }
+  for (int t = 0; t < T; ++t) pthread_join(th[t], NULL);
+  /* (2c) per group: the runs of the output against the input's keys */
+  int64_t next = 0;
+  for (int t = 0; t < T; ++t) {
+    mj[t].kout = kout; mj[t].kbytes = kbytes; mj[t].start = start;
+    mj[t].grouped = grouped; mj[t].next = &next;
+    pthread_create(&th[t], NULL, csk_match_main, &mj[t]);
+  }
+  for (int t = 0; t < T; ++t) pthread_join(th[t], NULL);
+  for (int t = 0; t < T; ++t) {
+    if (mj[t].bad < 0) { result = -2; goto done; }
+    if (mj[t].bad > 0 && (result < 0 || mj[t].bad - 1 < result)) result = mj[t].bad - 1;
+  }
+done:
+  free(cnt); free(start); free(grouped); free(cj); free(sj); free(mj); free(th);
+  return result;
 }
 
 /* ------------------------------------------------------------------------ */

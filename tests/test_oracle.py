@@ -460,6 +460,12 @@ MUTANTS = {
     # stable position counts ties after j as well
     "position_ties": ("c += (ki < kj) || (ki == kj && i < j);",
                       "c += (ki < kj) || (ki == kj && i <= j);"),
+    # key-only check: a run may take more input keys than it is long
+    "run_overuse": ("if (lo == r || rk[lo] != k || rlen[lo] == 0) ok = 0;",
+                    "if (lo == r || rk[lo] != k) ok = 0;"),
+    # key-only check: the run search finds the first run above the key
+    "run_upper_bound": ("if (rk[mid] < k) lo = mid + 1; else hi = mid;",
+                        "if (rk[mid] <= k) lo = mid + 1; else hi = mid;"),
 }
 
 
@@ -476,6 +482,7 @@ def _run_pins():
     test_golden_overflow_bucket_example()
     test_dtmerge_equals_stable_sort(3)
     test_dtmerge_equals_stable_sort(400)
+    test_check_sorted_keys_brute_force(W32)
 
 
 def test_pins_pass_on_the_oracle():
@@ -544,6 +551,59 @@ def test_check_stable_accepts_exactly_the_stable_sort(dtype):
     ix = io.copy()
     ix[-1] = n
     assert oracle.check_stable(keys, ko, ix) == n - 1
+
+
+@pytest.mark.parametrize("dtype", [W32, W64])
+def test_check_sorted_keys_brute_force(dtype):
+    # every candidate output of every tiny input, over keys from four
+    # different top-16-bit groups: exactly the sorted input passes
+    top = int(np.iinfo(dtype).max)
+    half = 1 << (8 * np.dtype(dtype).itemsize - 1)
+    alphabet = [0, 1, half, top]
+    for n in range(0, 4):
+        for combo in itertools.product(alphabet, repeat=n):
+            keys = np.array(combo, dtype=dtype)
+            want = sorted(combo)
+            for cand in itertools.product(alphabet, repeat=n):
+                got = oracle.check_sorted_keys(keys, np.array(cand, dtype=dtype), nthreads=1)
+                assert (got == -1) == (list(cand) == want), (combo, cand, got)
+
+
+@pytest.mark.parametrize("dtype", [W32, W64])
+def test_check_sorted_keys_catches_wrong_outputs(dtype):
+    # the key-only checker against numpy's sort and plausible wrong outputs
+    n = 200_003
+    keys = gen.family("zipf1.2hash" if dtype == W64 else "zipf1.0", n, dtype, seed=19)
+    ko = np.sort(keys)
+    assert oracle.check_sorted_keys(keys, ko) == -1
+    assert oracle.check_sorted_keys(keys, ko, nthreads=3) == -1
+    # the input itself (unsorted)
+    assert oracle.check_sorted_keys(keys, keys) >= 0
+    # two neighbours of different keys swapped
+    j = int(np.where(ko[1:] != ko[:-1])[0][0])
+    kb = ko.copy()
+    kb[j], kb[j + 1] = kb[j + 1], kb[j]
+    assert oracle.check_sorted_keys(keys, kb) == j
+    # a run one longer and the next one shorter, order kept (same group)
+    kr = ko.copy()
+    kr[j + 1] = kr[j]
+    if (int(ko[j]) >> 16) == (int(ko[j + 1]) >> 16) or dtype == W64:
+        assert oracle.check_sorted_keys(keys, kr) >= 0
+    # one key replaced by a neighbouring value that the input lacks
+    ks = ko.copy()
+    absent = int(ko[-1]) - 1
+    while absent in set(ko[-50:].tolist()):
+        absent -= 1
+    ks[-1] = absent
+    ks.sort()
+    assert oracle.check_sorted_keys(keys, ks) >= 0
+    # the largest key moved to another top-16-bit group, order kept
+    kg = ko.copy()
+    kg[-1] = np.iinfo(dtype).max if int(ko[-1]) != np.iinfo(dtype).max else 0
+    kg.sort()
+    assert oracle.check_sorted_keys(keys, kg) >= 0
+    # every key one larger
+    assert oracle.check_sorted_keys(keys, ko + dtype(1)) >= 0
 
 
 def test_edge_list_generator():
