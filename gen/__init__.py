@@ -169,11 +169,17 @@ def segmented_layout(nseg=4096, lo=100.0, hi=1e7, seed=1, total=None):
     return off, fam
 
 
-def fill_segmented_u32(keys_ptr, vals_ptr, offsets, family, seed=1, nthreads=0):
+def fill_segmented_u32(keys_ptr, vals_ptr, offsets, family, seed=1, nthreads=0,
+                       first_segment=0, last_segment=None):
     """Keys of array s: uniform u32 or Zipf(1.0) ranks - 1, from the stream
-    seeded with seed*65536 + s; values: index within the array."""
-    for s in range(len(offsets) - 1):
-        a, b = int(offsets[s]), int(offsets[s + 1])
+    seeded with seed*65536 + s; values: index within the array.  With
+    first_segment / last_segment only arrays [first, last) are filled, and
+    keys_ptr / vals_ptr point at the first one's first record."""
+    if last_segment is None:
+        last_segment = len(offsets) - 1
+    a0 = int(offsets[first_segment])
+    for s in range(first_segment, last_segment):
+        a, b = int(offsets[s]) - a0, int(offsets[s + 1]) - a0
         if b <= a:
             continue
         if family[s]:

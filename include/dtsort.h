@@ -325,9 +325,9 @@ DTSORT_API dtsort_status dtsort_autotune(dtsort_handle h, dtsort_op op, const vo
 /* ---- sorting without any allocation ---------------------------------------
  * The paper has no counterpart of this entry point.  It serves callers that
  * may not allocate device memory at call time and cannot provide a workspace
- * either: code running while a CUDA stream is captured, plugin or callback
- * code that gets a stream from a host framework owning all device memory,
- * real-time pipelines that forbid allocation after start-up.
+ * either: plugin or callback code that gets a stream from a host framework
+ * owning all device memory, real-time pipelines that forbid allocation after
+ * start-up.
  *
  * Same operation as dtsort_u32_kv (stable sort of keys[0..n) with values
  * alongside, in place, default options), but every temporary lives in one
@@ -337,7 +337,11 @@ DTSORT_API dtsort_status dtsort_autotune(dtsort_handle h, dtsort_op op, const vo
  * DTSORT_NOALLOC_MAX_N (larger n returns DTSORT_ERR_INVALID_ARG without
  * launching).  keys/values: device pointers on the current device, 4-byte
  * aligned.  device_status: optional device int32 the sort latches its device
- * status into (0 = OK; cleared at the start of the call); NULL to ignore.
+ * status into (0 = OK; cleared at the start of the call).  With NULL the
+ * status goes to a word inside the static array that the next call clears:
+ * a device-side failure (a bounded wait that ran out, a failed self-check,
+ * both leaving the records unsorted) then cannot be observed, so pass a
+ * word whenever the result matters.
  * The first call on a device performs a one-time set-up on that device
  * (looks up the array's device address, sets the kernel's shared-memory
  * limit); make that first call before any stream capture.  All calls share

@@ -1,8 +1,8 @@
 // dtsort_u32_kv_noalloc: the 32-bit key/value sort for callers that cannot
 // allocate device memory and cannot hand over a workspace either -- for
-// example code that runs while a CUDA stream is being captured, plugin or
-// callback code that receives a stream from a host framework owning all
-// device memory, or real-time pipelines that forbid allocations after start.
+// example plugin or callback code that receives a stream from a host
+// framework owning all device memory, or real-time pipelines that forbid
+// allocations after start-up.
 //
 // Everything the sort needs beyond the caller's keys and values (the second
 // copy of keys and values, the per-level tables, the control block) lives in

@@ -45,6 +45,119 @@ def test_c4_shape_parity(G):
     gpu_util.assert_same(gk, gv, ek, ev)
 
 
+@pytest.fixture(scope="module")
+def c4_bench_shape():
+    # the benchmark's batch: 4096 arrays, sizes log-uniform in [100, 10^7]
+    # scaled to a 2*10^8 total (the largest arrays hold ~10^6 records and
+    # take distribution levels), each uniform or Zipf(1.0); seed 1
+    keys, vals, off = c4_input(2e8, hi=1e7)
+    ek, ev = oracle.stable_sort_segmented(keys, vals, off)
+    return keys, vals, off, ek, ev
+
+
+def test_c4_benchmark_shape_parity(G, c4_bench_shape):
+    keys, vals, off, ek, ev = c4_bench_shape
+    assert np.diff(off).max() > 500_000
+    gk, gv = G.sort(keys, vals, off)
+    gpu_util.assert_same(gk, gv, ek, ev)
+
+
+def test_c4_benchmark_shape_graph_replay(G, c4_bench_shape):
+    # what bench.py --workload segmented --graph times: the call captured
+    # once, replayed on restored inputs
+    keys, vals, off, ek, ev = c4_bench_shape
+    n = len(keys)
+    nseg = len(off) - 1
+    pk = gpu_util.to_dev(keys, torch, G.dev)
+    pv = gpu_util.to_dev(vals, torch, G.dev)
+    k, v = pk.clone(), pv.clone()
+    o = torch.from_numpy(off).to(G.dev)
+    G.workspace(dts.DTSORT_OP_U32_KV, n, nseg)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        st = G.launch(k, v, n, dts.DTSORT_OP_U32_KV, o, nseg)
+    assert st == dts.DTSORT_OK
+    for _ in range(2):
+        k.copy_(pk)
+        v.copy_(pv)
+        graph.replay()
+        torch.cuda.synchronize()
+        assert G.device_status() == dts.DTSORT_OK
+        gpu_util.assert_same(gpu_util.from_dev(k, np.uint32), gpu_util.from_dev(v, np.uint32),
+                             ek, ev)
+    del graph, k, v, pk, pv
+    G.ws = None
+    torch.cuda.empty_cache()
+
+
+def _segment_chunks(off, limit):
+    """Runs [s0, s1) of whole arrays holding at most `limit` records (or one
+    array)."""
+    nseg = len(off) - 1
+    s0 = 0
+    while s0 < nseg:
+        s1 = s0 + 1
+        while s1 < nseg and off[s1 + 1] - off[s0] <= limit:
+            s1 += 1
+        yield s0, s1
+        s0 = s1
+
+
+@pytest.mark.slow
+def test_c4_literal_sizes_per_segment(G):
+    # the batch as drawn (3.53*10^9 records; the largest arrays near 10^7):
+    # generated, uploaded and checked a run of arrays at a time so that the
+    # host holds at most ~2.5*10^8 records; every array's output is checked
+    # against the definition (oracle.check_stable: values are the index
+    # within the array), and the largest array's sampled records against
+    # the oracle's position formula
+    off, fam = gen.segmented_layout(nseg=4096, lo=100, hi=1e7, seed=1, total=None)
+    n = int(off[-1])
+    nseg = len(off) - 1
+    assert n > 3_000_000_000
+    k = torch.empty(n, dtype=torch.int32, device=G.dev)
+    v = torch.empty(n, dtype=torch.int32, device=G.dev)
+    limit = 250_000_000
+
+    def host_chunk(s0, s1):
+        m = int(off[s1] - off[s0])
+        hk = np.empty(m, dtype=np.uint32)
+        hv = np.empty(m, dtype=np.uint32)
+        gen.fill_segmented_u32(hk.ctypes.data, hv.ctypes.data, off, fam, seed=1,
+                               first_segment=s0, last_segment=s1)
+        return hk, hv
+
+    for s0, s1 in _segment_chunks(off, limit):
+        hk, hv = host_chunk(s0, s1)
+        a, b = int(off[s0]), int(off[s1])
+        k[a:b].copy_(torch.from_numpy(hk.view(np.int32)))
+        v[a:b].copy_(torch.from_numpy(hv.view(np.int32)))
+    o = torch.from_numpy(off).to(G.dev)
+    st = G.launch(k, v, n, dts.DTSORT_OP_U32_KV, o, nseg)
+    assert st == dts.DTSORT_OK
+    assert G.device_status() == dts.DTSORT_OK
+    G.ws = None
+    torch.cuda.empty_cache()
+    big = int(np.argmax(np.diff(off)))
+    for s0, s1 in _segment_chunks(off, limit):
+        hk, _ = host_chunk(s0, s1)
+        a, b = int(off[s0]), int(off[s1])
+        gk = k[a:b].cpu().numpy().view(np.uint32)
+        gv = v[a:b].cpu().numpy().view(np.uint32)
+        for s in range(s0, s1):
+            x, y = int(off[s] - off[s0]), int(off[s + 1] - off[s0])
+            if y > x:
+                r = oracle.check_stable(hk[x:y], gk[x:y], gv[x:y])
+                assert r == -1, "array %d (size %d): first failing slot %d" % (s, y - x, r)
+            if s == big:
+                js = np.random.RandomState(8).randint(0, y - x, size=16).astype(np.int64)
+                pos = oracle.stable_positions(hk[x:y], js)
+                np.testing.assert_array_equal(gv[x:y][pos], js.astype(np.uint32))
+    del k, v, o
+    torch.cuda.empty_cache()
+
+
 def test_c4_key_only_and_u64(G):
     keys, vals, off = c4_input(3e6, seed=2, nseg=700)
     gk, _ = G.sort(keys, None, off)

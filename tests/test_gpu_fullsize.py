@@ -1,10 +1,13 @@
-"""Parity at the benchmark's full size (10^9 records), in the launch sequence
-bench.py times (the default options: the predicted levels as one launch per
-phase, then the persistent kernel).  The oracle cannot sort 10^9 records in
-seconds, so each output is checked against the definition of the stable sort
-(oracle.check_stable: (key, original index) strictly increasing, the indices a
-permutation, every key the input's key at its index — exactly one output
-passes) and 16 sampled records against the oracle's own position formula."""
+"""Parity at the benchmark's full size (10^9 records, and the 2*10^9 point of
+the size sweep), in the launch sequence bench.py times (the default options:
+the predicted levels as one launch per phase, then the persistent kernel).
+The oracle cannot sort 10^9 records in seconds, so each output is checked
+against the definition of the stable sort (oracle.check_stable: (key,
+original index) strictly increasing, the indices a permutation, every key the
+input's key at its index — exactly one output passes) and 16 sampled records
+against the oracle's own position formula.  Key-only outputs are checked
+against the key-only definition (oracle.check_sorted_keys: non-decreasing,
+and every key value exactly as often as in the input)."""
 import numpy as np
 import pytest
 
@@ -67,3 +70,42 @@ def test_full_learned_mixture(G):
     # lives with the learned tests)
     st = check_full(G, "skewmix", np.uint64, bucketing=dts.DTSORT_BUCKETING_LEARNED_ALWAYS)
     assert st["learned_zones_used"] == 1
+
+
+@pytest.mark.parametrize("dtype,name", [(np.uint32, "uniform"), (np.uint32, "zipf1.2"),
+                                        (np.uint64, "uniform"), (np.uint64, "heavymix")])
+def test_full_key_only(G, dtype, name):
+    # key-only sorts have their own base case (64-bit keys: 6144 records per
+    # bucket) and scatter counters; bench.py --op u32 / u64 times these
+    keys = gen.family(name, N, dtype, seed=1)
+    gk, _ = G.sort(keys)
+    st = G.stats()
+    assert st["status"] == 0
+    assert oracle.check_sorted_keys(keys, gk) == -1
+    if name == "uniform":
+        assert st["levels"] == 2
+    G.ws = None
+
+
+def test_size_sweep_top_point_2e9(G):
+    # the largest point of the size sweep: 2*10^9 u32 key/value pairs need a
+    # third distribution level; values = original index, made on the device
+    n = 2 * N
+    keys = gen.family("uniform", n, np.uint32, seed=1)
+    k = gpu_util.to_dev(keys, torch, G.dev)
+    v = torch.arange(n, dtype=torch.int64, device=G.dev).to(torch.int32)
+    st = G.launch(k, v, n, dts.DTSORT_OP_U32_KV)
+    assert st == dts.DTSORT_OK
+    assert G.device_status() == dts.DTSORT_OK
+    stats = G.stats()
+    assert stats["levels"] == 3
+    G.ws = None
+    gk = gpu_util.from_dev(k, np.uint32)
+    del k
+    gv = gpu_util.from_dev(v, np.uint32)
+    del v
+    torch.cuda.empty_cache()
+    assert oracle.check_stable(keys, gk, gv) == -1
+    js = np.random.RandomState(6).randint(0, n, size=16).astype(np.int64)
+    pos = oracle.stable_positions(keys, js)
+    np.testing.assert_array_equal(gv[pos], js.astype(np.uint32))

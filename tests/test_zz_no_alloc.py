@@ -1,17 +1,19 @@
 """The allocation-free entry point dtsort_u32_kv_noalloc.
 
-It exists for callers that may not allocate device memory when they sort
-(stream capture in progress, plugin/callback code inside a framework that owns
-all device memory, real-time pipelines): its temporaries live in a static
-device array inside the library.  Here it must give exactly what the regular
-entry point dtsort_u32_kv gives, on two calls in a row (the static array keeps
-the previous call's contents), and refuse sizes above its maximum.  This file
-is collected last on purpose.
+It exists for callers that may not allocate device memory when they sort:
+plugin or callback code handed a stream by a host framework that owns all
+device memory, or real-time pipelines that forbid allocation after start-up.
+Its temporaries live in a static device array inside the library.  Here it
+must give exactly what the regular entry point dtsort_u32_kv gives, and what
+the CPU oracle gives, on two calls in a row (the static array keeps the
+previous call's contents), and refuse sizes above its maximum.  This file is
+collected last on purpose.
 """
 import numpy as np
 import pytest
 
 import gen
+import oracle
 
 pytestmark = pytest.mark.gpu
 
@@ -59,7 +61,7 @@ def _noalloc(keys, vals, dev):
     return k.cpu().numpy().view(np.uint32), v.cpu().numpy().view(np.uint32)
 
 
-def test_noalloc_matches_regular_entry_point_twice(dev):
+def test_noalloc_matches_regular_entry_point_and_oracle_twice(dev):
     cases = [("zipf1.2", dts.DTSORT_NOALLOC_MAX_N, 3),
              ("uniform", 777_777, 4)]
     for name, n, seed in cases:  # two calls in a row share the static array
@@ -69,6 +71,9 @@ def test_noalloc_matches_regular_entry_point_twice(dev):
         nk, nv = _noalloc(keys, vals, dev)
         np.testing.assert_array_equal(nk, rk)
         np.testing.assert_array_equal(nv, rv)
+        ek, ev = oracle.stable_sort(keys, vals)
+        np.testing.assert_array_equal(nk, ek)
+        np.testing.assert_array_equal(nv, ev)
 
 
 def test_noalloc_refuses_sizes_above_its_maximum(dev):
