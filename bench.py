@@ -255,6 +255,16 @@ def single_config(args, world, tuned=None):
             "parallelism": "replicas" if world > 1 else "single"}
 
 
+def reference_config(args, world, sample):
+    """The reference arm's config: the same workload, of which the CPU oracle
+    sorts the first `sample` records per step (a bounded sample)."""
+    cfg = single_config(args, world)
+    if sample < args.n:
+        cfg["workload"] += " (the CPU oracle sorts its first %d records per step)" % sample
+        cfg["sample_n"] = sample
+    return cfg
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -273,7 +283,7 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": args.op, "data": "synthetic",
-            "config": single_config(args, world),
+            "config": reference_config(args, world, sample),
             "impl": "reference",
             "cpu_baseline": {"value": value, "unit": "keys/s", "cores": cores,
                              "kind": "oracle",
