@@ -70,6 +70,10 @@ def parse():
                     help="run the autotuner on the workload first and use its choice")
     ap.add_argument("--heavy", default="on", choices=["on", "off"],
                     help="off: no heavy-key detection (the paper's 'Plain' ablation)")
+    ap.add_argument("--parallel", default="replicas", choices=["replicas", "sharded"],
+                    help="N > 1: independent replicas, or one array of N*n records "
+                         "sharded over the ranks (sample, partition, one all-to-all, "
+                         "local sorts)")
     ap.add_argument("--merge", default="dovetail", choices=["dovetail", "generic"],
                     help="generic: merge-path merging of the heavy zones instead of "
                          "dovetail merging (the paper's merge ablation)")
@@ -658,12 +662,92 @@ def run_segmented(args):
     return 0
 
 
+def run_sharded(args):
+    """One array of world * n records, rank r holding records [r n, (r+1) n)
+    of the seeded stream; one step = the whole sharded sort (sample, gather,
+    splitters, partition, one all-to-all, local sort); max over ranks."""
+    import torch
+    import torch.distributed as tdist
+
+    import gen
+    import paper_2401_00710_gb300 as dts
+    from paper_2401_00710_gb300 import sharded
+
+    rank, world, local = dist_env()
+    tdist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    kd = key_dtype(args.op)
+    kbytes = np.dtype(kd).itemsize
+    has_v = args.op.endswith("kv")
+    n = args.n
+    tdt = torch.int32 if kbytes == 4 else torch.int64
+    table = gen.U32_FAMILIES if kbytes == 4 else gen.U64_FAMILIES
+    kind, _, p1, p2 = table[args.dist]
+    if p1 is None:
+        p1 = 10.0 / max(n * world, 1)
+    hk = torch.empty(n, dtype=tdt, pin_memory=True)
+    gen.fill_keys(hk.data_ptr(), n, kind, kbytes, args.seed, p1, p2, first=rank * n)
+    pk = hk.to(dev)
+    pv = None
+    if has_v:
+        hv = torch.empty(n, dtype=tdt, pin_memory=True)
+        gen.fill_iota(hv.data_ptr(), n, kbytes, first=rank * n)
+        pv = hv.to(dev)
+    ops = sharded.GpuShardOps(dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        k = pk.clone()
+        v = pv.clone() if has_v else None
+        torch.cuda.synchronize(dev)
+        tdist.barrier()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        res = sharded.sharded_sort(k, v, ops, seed=args.seed)
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        return a.elapsed_time(b), res
+
+    for _ in range(args.warmup):
+        step()
+    with ClockSampler(local) as clk:
+        ms = [step()[0] for _ in range(args.steps)]
+    ms_step = replica_ms(sum(ms) / len(ms), world, dev)
+    if rank != 0:
+        tdist.destroy_process_group()
+        return 0
+    peak, peak_kind = peaks()
+    achieved = B_ALG[args.op] * n / (ms_step / 1e3) / 1e9
+    cfg = single_config(args, world)
+    cfg["workload"] = ("stable sort of one array of %d records sharded over %d GPUs, %s, "
+                       "keys %s seed %d, values = global index" % (n * world, world, args.op,
+                                                                   args.dist, args.seed))
+    cfg["parallelism"] = "sharded: sample, partition, one all-to-all (NCCL), local sort"
+    line = {"metric": METRIC, "value": n * world / (ms_step / 1e3), "unit": "keys/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": args.op, "data": "synthetic", "config": cfg,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+                         "bytes_per_record": B_ALG[args.op],
+                         "kernel": "one rank's share of the sharded sort (algorithmic bytes "
+                                   "of its n records / step time, exchange included)"},
+            "gpu_launches": None, "clocks": clk.summary(), "e2e": None, "ms_steps": ms}
+    print(json.dumps(line), flush=True)
+    tdist.destroy_process_group()
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "segmented":
         return run_segmented(args)
+    if args.parallel == "sharded" and dist_env()[1] > 1:
+        return run_sharded(args)
     return run_ours(args)
 
 

@@ -322,6 +322,78 @@ DTSORT_API dtsort_status dtsort_autotune(dtsort_handle h, dtsort_op op, const vo
                                          size_t scratch_bytes, dtsort_stream stream,
                                          dtsort_options *best_out);
 
+/* ---- sorting an array sharded over several GPUs ----------------------------
+ * The rank-local steps of a sort with one exchange (no counterpart in the
+ * paper's single-machine setting; it applies the distribution step of the
+ * paper's counting sort (Sec. 2 preliminaries, "Counting Sort"; Alg. 2 step
+ * 2) with one bucket per rank).  P ranks hold contiguous, index-ordered
+ * shards of one array: rank r holds global records [gidx0_r, gidx0_r + n_r).
+ * The stable order of the array is the order of the pairs (key, global
+ * index) (Sec. 2.3), so:
+ *   1. every rank draws a sample of such pairs (dtsort_shard_sample); the
+ *      caller gathers all samples on every rank;
+ *   2. dtsort_shard_splitters picks P-1 splitters from the gathered sample;
+ *   3. every rank partitions its shard stably into P consecutive ranges,
+ *      range p = the records with p splitters <= (key, global index)
+ *      (dtsort_shard_partition); a key duplicated across a splitter is split
+ *      by global index, which keeps the ranges balanced;
+ *   4. the caller exchanges the ranges with one all-to-all (range p to rank
+ *      p, received runs concatenated in source-rank order, i.e. in global
+ *      index order);
+ *   5. rank p sorts what it received with dtsort_u32[_kv]/dtsort_u64[_kv]
+ *      and then holds the p-th consecutive part of the sorted array.
+ * Keys compare as unsigned; 32-bit keys are widened to 64 bits in samples
+ * and splitters. */
+#define DTSORT_SHARD_MAX_PARTS 64
+
+/* Draws `count` samples of the shard keys[0..n_local) (device, key_bytes 4 or
+ * 8), uniformly with replacement: sample i is the record at position
+ * x_i mod n_local, x_i the i-th output of SplitMix64 (Steele, Lea, Flood
+ * 2014) started from seed ^ fmix64(gidx0 + 0x9E3779B97F4A7C15).  Writes its
+ * key (widened to 64 bits) to sample_keys[i] and gidx0 + position to
+ * sample_gidx[i] (device arrays, 8-byte aligned).  count = 0 is a no-op;
+ * count > 0 needs n_local > 0.  Stream-ordered; INVALID_ARG on bad
+ * arguments, DTSORT_ERR_CUDA if the launch fails. */
+DTSORT_API dtsort_status dtsort_shard_sample(const void *keys, int key_bytes, int64_t n_local,
+                                             int64_t gidx0, uint64_t seed, int64_t count,
+                                             uint64_t *sample_keys, int64_t *sample_gidx,
+                                             dtsort_stream stream);
+
+/* Host only (no device, no stream): sorts the m gathered sample pairs
+ * (sample_keys[i], sample_gidx[i]) (host arrays) and writes splitter j-1 =
+ * the pair of rank floor(j m / parts), j = 1..parts-1, into split_keys /
+ * split_gidx (host arrays of parts-1 entries, increasing).  With m = 0 every
+ * splitter is (2^64-1, INT64_MAX): all records fall into range 0.
+ * parts in [1, DTSORT_SHARD_MAX_PARTS]. */
+DTSORT_API dtsort_status dtsort_shard_splitters(const uint64_t *sample_keys,
+                                                const int64_t *sample_gidx, int64_t m, int parts,
+                                                uint64_t *split_keys, int64_t *split_gidx);
+
+/* Workspace of dtsort_shard_partition for n_local records and `parts`
+ * ranges (256 + 8 * rows * parts bytes, rows <= 4096). */
+DTSORT_API dtsort_status dtsort_shard_partition_workspace_bytes(int64_t n_local, int parts,
+                                                                size_t *bytes);
+
+/* Stable partition of the shard keys/values[0..n_local) (device; values NULL
+ * for key-only; record i has global index gidx0 + i) into `parts`
+ * consecutive ranges of out_keys/out_values (device, n_local records, not
+ * overlapping the input): range p holds, in index order, the records with
+ * exactly p of the splitters (split_keys[j], split_gidx[j]) (device, parts-1
+ * increasing pairs) <= (key, gidx0 + i).  counts (device int64[parts])
+ * receives each range's size.  ws: device, 256-byte aligned, at least
+ * dtsort_shard_partition_workspace_bytes.  device_status (optional, device
+ * int32): cleared, then set to DTSORT_ERR_INTERNAL if a self-check finds a
+ * slot outside the shard (nothing is written there); NULL: kept in the
+ * workspace, not observable.  Pointers aligned to the key width.
+ * Stream-ordered; INVALID_ARG / WORKSPACE_TOO_SMALL / DTSORT_ERR_CUDA. */
+DTSORT_API dtsort_status dtsort_shard_partition(const void *keys, const void *values,
+                                                int key_bytes, int64_t n_local, int64_t gidx0,
+                                                const uint64_t *split_keys,
+                                                const int64_t *split_gidx, int parts,
+                                                void *out_keys, void *out_values,
+                                                int64_t *counts, void *ws, size_t ws_bytes,
+                                                int32_t *device_status, dtsort_stream stream);
+
 /* ---- sorting without any allocation ---------------------------------------
  * The paper has no counterpart of this entry point.  It serves callers that
  * may not allocate device memory at call time and cannot provide a workspace

@@ -37,7 +37,12 @@ EXPORTED = [
     "dtsort_last_device_error", "dtsort_get_stats", "dtsort_debug_sample",
     "dtsort_u32_kv_noalloc", "dtsort_autotune", "dtsort_autotune_scratch_bytes",
     "dtsort_mlp_forward", "dtsort_mlp_grad", "dtsort_mlp_adam", "dtsort_mlp_train",
+    "dtsort_shard_sample", "dtsort_shard_splitters", "dtsort_shard_partition_workspace_bytes",
+    "dtsort_shard_partition",
 ]
+
+# most ranges of a sharded sort (DTSORT_SHARD_MAX_PARTS in dtsort.h)
+DTSORT_SHARD_MAX_PARTS = 64
 
 # largest n of dtsort_u32_kv_noalloc (DTSORT_NOALLOC_MAX_N in dtsort.h)
 DTSORT_NOALLOC_MAX_N = 1 << 20
@@ -169,6 +174,13 @@ def _declare(L):
                                                 ctypes.POINTER(_SZ)]
     L.dtsort_autotune.argtypes = [_H, ctypes.c_int, _P, _P, _P, _I64, _I64, _P, _SZ,
                                   _P, ctypes.POINTER(dtsort_options)]
+    L.dtsort_shard_sample.argtypes = [_P, ctypes.c_int, _I64, _I64, ctypes.c_uint64, _I64,
+                                      _P, _P, _P]
+    L.dtsort_shard_splitters.argtypes = [_P, _P, _I64, ctypes.c_int, _P, _P]
+    L.dtsort_shard_partition_workspace_bytes.argtypes = [_I64, ctypes.c_int,
+                                                         ctypes.POINTER(_SZ)]
+    L.dtsort_shard_partition.argtypes = [_P, _P, ctypes.c_int, _I64, _I64, _P, _P,
+                                         ctypes.c_int, _P, _P, _P, _P, _SZ, _P, _P]
     for name in EXPORTED:
         if name != "dtsort_status_string":
             getattr(L, name).restype = _ST
@@ -322,6 +334,34 @@ def dtsort_autotune(h, op, keys, values, offsets, num_segments, n, scratch,
 def dtsort_u32_kv_noalloc(keys, values, n, device_status=None, stream=0):
     """The allocation-free 32-bit key/value sort (n <= DTSORT_NOALLOC_MAX_N)."""
     return lib().dtsort_u32_kv_noalloc(keys, values, n, device_status, stream or None)
+
+
+def dtsort_shard_sample(keys, key_bytes, n_local, gidx0, seed, count, sample_keys,
+                        sample_gidx, stream=0):
+    return lib().dtsort_shard_sample(keys, key_bytes, n_local, gidx0, seed, count,
+                                     sample_keys, sample_gidx, stream or None)
+
+
+def dtsort_shard_splitters(sample_keys, sample_gidx, m, parts, split_keys, split_gidx):
+    """Host arrays (pointers) in and out."""
+    return lib().dtsort_shard_splitters(sample_keys, sample_gidx, m, parts, split_keys,
+                                        split_gidx)
+
+
+def dtsort_shard_partition_workspace_bytes(n_local, parts):
+    b = _SZ(0)
+    _check(lib().dtsort_shard_partition_workspace_bytes(int(n_local), int(parts),
+                                                        ctypes.byref(b)),
+           "dtsort_shard_partition_workspace_bytes")
+    return b.value
+
+
+def dtsort_shard_partition(keys, values, key_bytes, n_local, gidx0, split_keys, split_gidx,
+                           parts, out_keys, out_values, counts, ws, ws_bytes,
+                           device_status=None, stream=0):
+    return lib().dtsort_shard_partition(keys, values, key_bytes, n_local, gidx0, split_keys,
+                                        split_gidx, parts, out_keys, out_values, counts, ws,
+                                        ws_bytes, device_status, stream or None)
 
 
 # ---- PyTorch convenience ----------------------------------------------------
