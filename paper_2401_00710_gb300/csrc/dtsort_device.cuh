@@ -265,6 +265,29 @@ __device__ __forceinline__ K ld_key(const K *p) {
   else return (K)__ldcg((const unsigned long long *)p);
 }
 
+// L2 eviction policy (createpolicy) for stores that carry a cache hint.  The
+// scatter writes each bucket's run a little per tile; its stores are kept
+// (evict last) so that a 32-byte sector left partly written by one tile is
+// more often still in L2 when the next tile completes it (evicted partly
+// written, it costs a read-modify-write of the sector in DRAM).  Measured on
+// 10^9 32-bit key/value pairs: the two scatters 15.5 -> 14.6 ms.  (Loads
+// marked evict-first as well lost: 18.8 ms.)
+__device__ __forceinline__ uint64_t l2_policy_evict_last() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+// A key-sized store with an L2 eviction policy.
+template <typename K>
+__device__ __forceinline__ void st_key_hint(K *p, K v, uint64_t pol) {
+  if constexpr (sizeof(K) == 4)
+    asm volatile("st.global.L2::cache_hint.b32 [%0], %1, %2;" ::"l"(p), "r"((uint32_t)v), "l"(pol)
+                 : "memory");
+  else
+    asm volatile("st.global.L2::cache_hint.b64 [%0], %1, %2;" ::"l"(p), "l"((uint64_t)v), "l"(pol)
+                 : "memory");
+}
+
 template <typename K>
 __device__ __forceinline__ uint32_t hash_slot(K key, int bits) {
   return (uint32_t)(((uint64_t)key * 0x9E3779B97F4A7C15ull) >> (64 - bits));

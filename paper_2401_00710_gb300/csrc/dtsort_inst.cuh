@@ -43,7 +43,7 @@ cudaError_t DTS_CAT(shape_, DTS_NAME)(KernelShape *out) {
     e = cudaFuncSetAttribute(pk[ph], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     int b = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, pk[ph], NT, sm);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, pk[ph], phase_threads(ph), sm);
     if (e != cudaSuccess) return e;
     out->phase_blocks[ph] = b < phase_min_blocks(ph) ? b : phase_min_blocks(ph);
   }
@@ -79,7 +79,7 @@ cudaError_t DTS_CAT(launch_, DTS_NAME)(const Params &P, int grid, int head, cons
       case KP_HIST: dtsort_phase_one<DTS_K, DTS_HV, KP_HIST><<<g, NT, smem, s>>>(P, level, prev); break;
       case KP_MSCAN: dtsort_phase_one<DTS_K, DTS_HV, KP_MSCAN><<<g, NT, smem, s>>>(P, level, prev); break;
       case KP_SCAN: dtsort_phase_one<DTS_K, DTS_HV, KP_SCAN><<<g, NT, smem, s>>>(P, level, prev); break;
-      case KP_SCATTER: dtsort_phase_one<DTS_K, DTS_HV, KP_SCATTER><<<g, NT, smem, s>>>(P, level, prev); break;
+      case KP_SCATTER: dtsort_phase_one<DTS_K, DTS_HV, KP_SCATTER><<<g, SCATTER_NT, smem, s>>>(P, level, prev); break;
       case KP_MERGE_PREP: dtsort_phase_one<DTS_K, DTS_HV, KP_MERGE_PREP><<<g, NT, smem, s>>>(P, level, prev); break;
       case KP_MERGE: dtsort_phase_one<DTS_K, DTS_HV, KP_MERGE><<<g, NT, smem, s>>>(P, level, prev); break;
       case KP_STATS: dtsort_phase_one<DTS_K, DTS_HV, KP_STATS><<<g, NT, smem, s>>>(P, level, prev); break;

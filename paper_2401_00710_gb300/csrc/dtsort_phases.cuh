@@ -64,29 +64,46 @@ struct Carve {
   }
 };
 
+// Threads of the per-phase scatter kernel: one CTA of 1024 per SM, tiles of
+// 1024 * ITEMS records.  Twice the records per tile give each bucket run of a
+// tile twice the length, so half as many partly written 32-byte sectors per
+// byte moved (each costs a DRAM read-modify-write when it leaves L2 before
+// the next tile completes it).  The persistent kernel scatters with NT.
+constexpr int SCATTER_NT = 1024;
+
 // Bytes of the scatter's staged tile (keys with their destinations, or keys
-// with their values).
-template <typename K, bool HV>
+// with their values) for CTAs of NTS threads.
+template <typename K, bool HV, int NTS = NT>
 __host__ __device__ constexpr int scatter_area() {
   using S = Shape<K, HV>;
-  constexpr int kd = S::TILE * (int)sizeof(K) + 4 * S::TILE;
-  constexpr int kv = HV ? 2 * S::TILE * (int)sizeof(K) : 0;
+  constexpr int tile = NTS * S::ITEMS;
+  constexpr int kd = tile * (int)sizeof(K) + 4 * tile;
+  constexpr int kv = HV ? 2 * tile * (int)sizeof(K) : 0;
   return kd > kv ? kd : kv;
+}
+
+// Dynamic shared memory of the scatter with CTAs of NTS threads (the arrays
+// phase_scatter carves, in its order, each 16-byte aligned).
+template <typename K, bool HV, int NTS = NT>
+constexpr size_t scatter_smem() {
+  constexpr int NWS = NTS / 32;
+  size_t sc = 0;
+  sc += 64 + sizeof(SegTables<K>);
+  sc += 16 + 4 * ((1 << GAMMA_HW) + 1);            // lid
+  sc += 16 + sizeof(K) * HASH_HW + 16 + 2 * HASH_HW;  // hash
+  sc += 16 + 4 * (size_t)NWS * NB_PAIR;            // warp counters
+  sc += 3 * (16 + 4 * NB_PAD);                     // tile offsets, bases
+  sc += 16 + 4 * (NWS + 1);                        // warp sums
+  sc += 16 + sizeof(K) * (1 << GAMMA_HW) + 16 + 4 * (LRN_TAB_N + 1);  // learned tables
+  sc += 16 + (size_t)scatter_area<K, HV, NTS>();   // staged tile
+  return sc + 256;
 }
 
 template <typename K, bool HV>
 constexpr size_t smem_bytes() {
   using S = Shape<K, HV>;
   // scatter
-  size_t sc = 0;
-  sc += 64 + sizeof(SegTables<K>);
-  sc += 16 + 4 * ((1 << GAMMA_HW) + 1);            // lid
-  sc += 16 + sizeof(K) * HASH_HW + 16 + 2 * HASH_HW;  // hash
-  sc += 16 + 4 * (size_t)NWARP * NB_PAIR;          // warp counters
-  sc += 3 * (16 + 4 * NB_PAD);                     // tile offsets, bases
-  sc += 16 + (size_t)scatter_area<K, HV>();        // staged tile
-  sc += 16 + 8 * (NWARP + 1) + 256;
-  sc += 16 + sizeof(K) * (1 << GAMMA_HW) + 16 + 4 * (LRN_TAB_N + 1);  // learned tables
+  const size_t sc = scatter_smem<K, HV, NT>();
   // base case
   size_t fin = 0;
   fin += 16 + (size_t)S::FIN_BYTES;
@@ -131,14 +148,19 @@ constexpr size_t phase_smem_bytes(int ph) {
       return dov > gen ? dov : gen;
     }
     case 11: return 256;                       // KP_STATS
-    default: return smem_bytes<K, HV>();       // scatter, base case
+    case 6: return scatter_smem<K, HV, SCATTER_NT>();  // KP_SCATTER
+    default: return smem_bytes<K, HV>();       // base case
   }
 }
 
+// Threads per CTA of each per-phase kernel.
+__host__ __device__ constexpr int phase_threads(int ph) { return ph == 6 ? SCATTER_NT : NT; }
+
 // CTAs per SM the per-phase kernels are built for: the light phases 3, the
-// scatter and the base case 2 (their shared memory allows no more).
+// base case 2, the scatter 1024 threads' worth (64 registers a thread; their
+// shared memory allows no more).
 __host__ __device__ constexpr int phase_min_blocks(int ph) {
-  return (ph >= 2 && ph <= 5) ? 3 : 2;
+  return (ph >= 2 && ph <= 5) ? 3 : (ph == 6 ? 1024 / SCATTER_NT : 2);
 }
 
 // ----------------------------------------------------------------- queues
@@ -768,9 +790,11 @@ __device__ void phase_scan(const Params &P, int level, unsigned char *smem) {
 // tile scan, then each warp's first slot per bucket (one barrier inside) |
 // barrier | stage | barrier | write-out (the warp counters are cleared
 // meanwhile) | barrier.
-template <typename K, bool HV>
+template <typename K, bool HV, int NTS = NT>
 __device__ void phase_scatter(const Params &P, int level, unsigned char *smem) {
   using S = Shape<K, HV>;
+  constexpr int NWS = NTS / 32;           // warps of this CTA
+  constexpr int TILE = NTS * S::ITEMS;    // records per tile
   Ctl *c = P.ctl;
   const int64_t nseg = min(ld_cg64(&c->nseg[level & 1]), (long long)P.maxseg);
   const int64_t nblocks = ld_cg64(&c->nblocks);
@@ -784,7 +808,7 @@ __device__ void phase_scatter(const Params &P, int level, unsigned char *smem) {
   int32_t *lid_s = cv.take<int32_t>((1 << GAMMA_HW) + 1);
   K *hk_s = cv.take<K>(HASH_HW);
   uint16_t *hid_s = cv.take<uint16_t>(HASH_HW);
-  unsigned *wc2 = cv.take<unsigned>(NWARP * NB_PAIR);  // warp counters, 16-bit pairs
+  unsigned *wc2 = cv.take<unsigned>(NWS * NB_PAIR);  // warp counters, 16-bit pairs
   // FOLD: the warps' counters become their first slots per bucket (tile
   // offset included), so staging reads one table instead of two; not for
   // 32-bit key/value pairs, whose scatter spills more with it (measured at
@@ -794,23 +818,23 @@ __device__ void phase_scatter(const Params &P, int level, unsigned char *smem) {
   unsigned *toff = cv.take<unsigned>(FOLD ? 1 : NB_PAD);
   unsigned *gbase = cv.take<unsigned>(NB_PAD);
   unsigned *base = cv.take<unsigned>(NB_PAD);
-  unsigned *sh = cv.take<unsigned>(NWARP + 1);
+  unsigned *sh = cv.take<unsigned>(NWS + 1);
   K *spl_s = cv.take<K>(1 << GAMMA_HW);
   float *tab_s = cv.take<float>(LRN_TAB_N + 1);
   // the staged tile: keys + destinations, or keys + values on the fast path
-  constexpr int AREA = scatter_area<K, HV>();
+  constexpr int AREA = scatter_area<K, HV, NTS>();
   unsigned char *area = cv.take<unsigned char>(AREA);
   K *stage = (K *)area;
-  unsigned *dest = (unsigned *)(area + S::TILE * sizeof(K));  // offset in the subproblem
+  unsigned *dest = (unsigned *)(area + TILE * sizeof(K));  // offset in the subproblem
   // the ranking's peer slots use the staging area too (cleared before each
   // tile is ranked, after the previous tile's write-out has finished)
-  static_assert(AREA >= 4 * NWARP * NB_PAD, "slots fit in the staging area");
+  static_assert(AREA >= 4 * NWS * NB_PAD, "slots fit in the staging area");
   unsigned *slots = (unsigned *)area;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   unsigned bad = 0;  // self-check: a slot or destination out of range, reported once
   unsigned *mywc = wc2 + w * NB_PAIR;
   unsigned *myslot = slots + w * NB_PAD;
-  for (int i = threadIdx.x; i < NWARP * NB_PAIR; i += NT) wc2[i] = 0u;
+  for (int i = threadIdx.x; i < NWS * NB_PAIR; i += NTS) wc2[i] = 0u;
   __syncthreads();
   const int64_t r0 = nblocks * blockIdx.x / gridDim.x;
   const int64_t r1 = nblocks * (blockIdx.x + 1) / gridDim.x;
@@ -836,18 +860,17 @@ __device__ void phase_scatter(const Params &P, int level, unsigned char *smem) {
     const BucketCtx X = bucket_ctx<K>(T);
     const int64_t lr = r - T.info.blk0;
     const unsigned *Xr = P.cmat + T.info.coff + lr * nb;  // this block's offsets
-    for (int b = threadIdx.x; b < nb; b += NT)
+    for (int b = threadIdx.x; b < nb; b += NTS)
       base[b] = (unsigned)(__ldcg((const long long *)&P.bstart[T.info.boff + b]) - T.start) +
                 __ldcg(Xr + b);
-    const int64_t b0 = T.start + lr * (int64_t)P.blk_tiles * S::TILE;
-    const int64_t brem = T.start + T.size - b0;
+    const int64_t blkrec = (int64_t)P.blk_tiles * S::TILE;  // records per row
+    const int64_t b0 = T.start + lr * blkrec;
+    const int64_t brem = T.start + T.size - b0 < blkrec ? T.start + T.size - b0 : blkrec;
     K *dseg = dst + T.start;
     K *vdseg = HV ? vdst + T.start : nullptr;
     const unsigned seg_size = (unsigned)T.size;
-    for (int sub = 0; sub < P.blk_tiles; ++sub) {
-      const int64_t tb = (int64_t)sub * S::TILE;
-      if (tb >= brem) break;
-      const int tn = brem - tb < S::TILE ? (int)(brem - tb) : S::TILE;
+    for (int64_t tb = 0; tb < brem; tb += TILE) {
+      const int tn = brem - tb < TILE ? (int)(brem - tb) : TILE;
       const int64_t tbase = b0 + tb;
       K key[S::ITEMS];
       unsigned br[S::ITEMS];  // bucket << 16 | rank within warp, later the slot
@@ -864,17 +887,17 @@ __device__ void phase_scatter(const Params &P, int level, unsigned char *smem) {
       // the next tile's keys (9.8 -> 9.0 ms)
       if (threadIdx.x == 0) {
         if constexpr (sizeof(K) == 8) {
-          prefetch_l2<K>(src, tbase + S::TILE, S::TILE, P.n);
-          if constexpr (HV) prefetch_l2<K>(vsrc, tbase, 2 * S::TILE, P.n);
+          prefetch_l2<K>(src, tbase + TILE, TILE, P.n);
+          if constexpr (HV) prefetch_l2<K>(vsrc, tbase, 2 * TILE, P.n);
         } else if constexpr (HV) {
-          prefetch_l2<K>(vsrc, tbase, S::TILE, P.n);
+          prefetch_l2<K>(vsrc, tbase, TILE, P.n);
         } else {
-          prefetch_l2<K>(src, tbase + S::TILE, S::TILE, P.n);
+          prefetch_l2<K>(src, tbase + TILE, TILE, P.n);
         }
       }
       {
         uint4 *z = (uint4 *)slots;
-        for (int i = threadIdx.x; i < NWARP * NB_PAD / 4; i += NT) z[i] = make_uint4(0, 0, 0, 0);
+        for (int i = threadIdx.x; i < NWS * NB_PAD / 4; i += NTS) z[i] = make_uint4(0, 0, 0, 0);
       }
       __syncthreads();
       if (fast) {
@@ -903,7 +926,7 @@ __device__ void phase_scatter(const Params &P, int level, unsigned char *smem) {
         unsigned tot2 = 0;
         if (p < npair) {
 #pragma unroll
-          for (int q = 0; q < NWARP; ++q) {
+          for (int q = 0; q < NWS; ++q) {
             const unsigned y = wc2[q * NB_PAIR + p];
             if constexpr (!FOLD) wc2[q * NB_PAIR + p] = tot2;  // exclusive prefix
             tot2 += y;
@@ -926,7 +949,7 @@ __device__ void phase_scatter(const Params &P, int level, unsigned char *smem) {
           if constexpr (FOLD) {
             unsigned run = off | ((off + c0) << 16);
 #pragma unroll
-            for (int q = 0; q < NWARP; ++q) {
+            for (int q = 0; q < NWS; ++q) {
               const unsigned y = wc2[q * NB_PAIR + p];
               wc2[q * NB_PAIR + p] = run;
               run += y;
@@ -946,7 +969,7 @@ __device__ void phase_scatter(const Params &P, int level, unsigned char *smem) {
         // keys and values staged side by side in bucket order; the write-out
         // takes each record's bucket again from its key (a digit), so no
         // destination array is kept and both arrays go out in one pass
-        K *stage_v = (K *)(area + S::TILE * sizeof(K));
+        K *stage_v = (K *)(area + TILE * sizeof(K));
 #pragma unroll
         for (int j = 0; j < S::ITEMS; ++j) {
           const int i = w * 32 * S::ITEMS + j * 32 + lane;
@@ -967,17 +990,18 @@ __device__ void phase_scatter(const Params &P, int level, unsigned char *smem) {
 #pragma unroll
           for (int j = 0; j < S::ITEMS; ++j) {
             const int i = w * 32 * S::ITEMS + j * 32 + lane;
-            if (i < tn && br[j] != 0xFFFFFFFFu) stage_v[br[j]] = ld_key<K>(vsrc + tbase + i);
+            if (i < tn && br[j] != 0xFFFFFFFFu)
+              stage_v[br[j]] = ld_key<K>(vsrc + tbase + i);
           }
         }
         __syncthreads();
-        for (int i = threadIdx.x; i < NWARP * NB_PAIR; i += NT) wc2[i] = 0u;
-        for (int q = threadIdx.x; q < tn; q += NT) {
+        for (int i = threadIdx.x; i < NWS * NB_PAIR; i += NTS) wc2[i] = 0u;
+        for (int q = threadIdx.x; q < tn; q += NTS) {
           const K k = stage[q];
           const unsigned d = gbase[fast_digit<K>(k, kbase, lo, gmask)] + (unsigned)q;
           if (d < seg_size) {
-            dseg[d] = k;
-            if constexpr (HV) vdseg[d] = stage_v[q];
+            st_key_hint<K>(dseg + d, k, l2_policy_evict_last());
+            if constexpr (HV) st_key_hint<K>(vdseg + d, stage_v[q], l2_policy_evict_last());
           } else {
             bad = 1u + d;
           }
@@ -1014,10 +1038,10 @@ __device__ void phase_scatter(const Params &P, int level, unsigned char *smem) {
         }
       }
       __syncthreads();
-      for (int i = threadIdx.x; i < NWARP * NB_PAIR; i += NT) wc2[i] = 0u;
-      for (int q = threadIdx.x; q < tn; q += NT) {
+      for (int i = threadIdx.x; i < NWS * NB_PAIR; i += NTS) wc2[i] = 0u;
+      for (int q = threadIdx.x; q < tn; q += NTS) {
         const unsigned d = dest[q];
-        if (d < seg_size) dseg[d] = stage[q];
+        if (d < seg_size) st_key_hint<K>(dseg + d, stage[q], l2_policy_evict_last());
         else bad = 1u + d;
       }
       if constexpr (HV) {
@@ -1028,9 +1052,9 @@ __device__ void phase_scatter(const Params &P, int level, unsigned char *smem) {
           if (i < tn) stage[br[j]] = val[j];
         }
         __syncthreads();
-        for (int q = threadIdx.x; q < tn; q += NT) {
+        for (int q = threadIdx.x; q < tn; q += NTS) {
           const unsigned d = dest[q];
-          if (d < seg_size) vdseg[d] = stage[q];
+          if (d < seg_size) st_key_hint<K>(vdseg + d, stage[q], l2_policy_evict_last());
         }
       }
       __syncthreads();
@@ -1971,6 +1995,8 @@ enum {
   KP_SEED = 0, KP_SETUP, KP_SAMPLE, KP_HIST, KP_MSCAN, KP_SCAN, KP_SCATTER, KP_FINISH,
   KP_CLOSE, KP_MERGE_PREP, KP_MERGE, KP_STATS
 };
+static_assert(KP_SAMPLE == 2 && KP_SCAN == 5 && KP_SCATTER == 6 && KP_STATS == 11,
+              "phase_smem_bytes, phase_threads and phase_min_blocks number the phases so");
 
 // One phase (all phases share one body, so that the persistent kernel and
 // the per-phase kernel are compiled alike).
@@ -2130,7 +2156,7 @@ __global__ void __launch_bounds__(NT, 2) dtsort_phase_kernel(const __grid_consta
 // records that the level is done.  prev_kind >= 0: the phase-time bucket the
 // time since the previous launch's start goes to.
 template <typename K, bool HV, int PH>
-__global__ void __launch_bounds__(NT, phase_min_blocks(PH))
+__global__ void __launch_bounds__(phase_threads(PH), phase_min_blocks(PH))
     dtsort_phase_one(const __grid_constant__ Params P, int level, int prev_kind) {
   Ctl *c = P.ctl;
   if (PH == KP_STATS) {  // after an error too: the status goes out with them
@@ -2160,7 +2186,7 @@ __global__ void __launch_bounds__(NT, phase_min_blocks(PH))
   else if constexpr (PH == KP_HIST) phase_hist<K, HV>(P, level, smem);
   else if constexpr (PH == KP_MSCAN) phase_mscan<K, HV>(P, level, smem);
   else if constexpr (PH == KP_SCAN) phase_scan<K, HV>(P, level, smem);
-  else if constexpr (PH == KP_SCATTER) phase_scatter<K, HV>(P, level, smem);
+  else if constexpr (PH == KP_SCATTER) phase_scatter<K, HV, SCATTER_NT>(P, level, smem);
   else if constexpr (PH == KP_MERGE_PREP) phase_merge_prep<K, HV>(P, level, smem);
   else if constexpr (PH == KP_MERGE) phase_merge<K, HV>(P, level, smem);
   else if constexpr (PH == KP_FINISH) {
