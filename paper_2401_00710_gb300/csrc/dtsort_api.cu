@@ -431,23 +431,34 @@ dtsort_status run_sort(dtsort_handle h, int op, void *keys, void *vals, const in
                                       w + L.lws, L.lws_bytes, s, false);
     if (st != DTSORT_OK) return st;
     const int steps = h->opt.learned_train_steps > 0 ? h->opt.learned_train_steps : 200;
-    if ((e = dts::lrn_features(smp, L.lrn_m, 8 * kb, x, t, nullptr, s)) != cudaSuccess ||
-        (e = dts::lrn_init(prm, prm + 352, prm + 704, lseed, nullptr, s)) != cudaSuccess ||
-        (e = dts::lrn_train(prm, prm + 352, prm + 704, x, t, L.lrn_m, steps, kLrnBatch, 1e-2f,
-                            (float *)(w + L.lpart), nullptr, s)) != cudaSuccess ||
-        (e = dts::lrn_splitters(prm, L.lrn_B, kb, w + L.lspl, (float *)(w + L.ltab), nullptr,
-                                s)) != cudaSuccess)
-      return DTSORT_ERR_CUDA;
-    h->launches += 4 + 2 * (int64_t)steps;  // gather, features, init, training, boundaries
-    // LEARNED: the device decides, from the sorted sample, whether the model's
-    // zones pay (level 0 reads its flag); ALWAYS: they are used
+    // LEARNED: the device decides, from the sorted sample, whether learned
+    // zones pay (level 0 reads its flag) -- first on zones at the sample's
+    // quantiles (the best any CDF model can give), before any training: when
+    // even those keep the digit zones, the model's features, training and
+    // boundaries return at once; otherwise once more on the trained model's
+    // zones.  ALWAYS: the model's zones are used.
     const bool decide = h->opt.bucketing == DTSORT_BUCKETING_LEARNED;
     int *on = decide ? (int *)(w + L.ldec) : nullptr;
     double *est = decide ? (double *)(w + L.ldec + 8) : nullptr;
+    const int gmx = std::min(o.gamma_max, dts::GAMMA_HW);
     if (decide) {
-      if ((e = dts::lrn_decide(smp, L.lrn_m, n, kb, L.lrn_B, w + L.lspl, L.cap, L.target,
-                               std::min(o.gamma_max, dts::GAMMA_HW), kLrnPenalty, on, est,
-                               s)) != cudaSuccess)
+      if ((e = dts::lrn_quantiles(smp, L.lrn_m, kb, L.lrn_B, w + L.lspl, s)) != cudaSuccess ||
+          (e = dts::lrn_decide(smp, L.lrn_m, n, kb, L.lrn_B, w + L.lspl, L.cap, L.target, gmx,
+                               kLrnPenalty, on, est, nullptr, s)) != cudaSuccess)
+        return DTSORT_ERR_CUDA;
+      h->launches += 2;
+    }
+    if ((e = dts::lrn_features(smp, L.lrn_m, 8 * kb, x, t, on, s)) != cudaSuccess ||
+        (e = dts::lrn_init(prm, prm + 352, prm + 704, lseed, on, s)) != cudaSuccess ||
+        (e = dts::lrn_train(prm, prm + 352, prm + 704, x, t, L.lrn_m, steps, kLrnBatch, 1e-2f,
+                            (float *)(w + L.lpart), on, s)) != cudaSuccess ||
+        (e = dts::lrn_splitters(prm, L.lrn_B, kb, w + L.lspl, (float *)(w + L.ltab), on,
+                                s)) != cudaSuccess)
+      return DTSORT_ERR_CUDA;
+    h->launches += 4 + 2 * (int64_t)steps;  // gather, features, init, training, boundaries
+    if (decide) {
+      if ((e = dts::lrn_decide(smp, L.lrn_m, n, kb, L.lrn_B, w + L.lspl, L.cap, L.target, gmx,
+                               kLrnPenalty, on, est, on, s)) != cudaSuccess)
         return DTSORT_ERR_CUDA;
       h->launches += 1;
     }

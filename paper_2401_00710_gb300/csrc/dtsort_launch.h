@@ -56,9 +56,13 @@ cudaError_t lrn_train(float *params, float *mom, float *vel, const float *x, con
                       cudaStream_t s);
 cudaError_t lrn_splitters(const float *params, int B, int kb, void *spl, float *tab,
                           const int *en, cudaStream_t s);
-// the device's decision whether learned zones pay (see lrn_decide_kernel)
+// the device's decision whether learned zones pay (see lrn_decide_kernel);
+// en: NULL, or an earlier decision that, when 0, stands
 cudaError_t lrn_decide(const uint64_t *sorted, int64_t m, int64_t n, int kb, int B,
                        const void *spl, int cap, int64_t target, int gmax, double penalty,
-                       int *on, double *est, cudaStream_t s);
+                       int *on, double *est, const int *en, cudaStream_t s);
+// zone lower bounds at the sorted sample's quantiles (lrn_quantile_kernel)
+cudaError_t lrn_quantiles(const uint64_t *sorted, int64_t m, int kb, int B, void *spl,
+                          cudaStream_t s);
 
 }  // namespace dts

@@ -97,13 +97,22 @@ cudaError_t lrn_splitters(const float *params, int B, int kb, void *spl, float *
 
 cudaError_t lrn_decide(const uint64_t *sorted, int64_t m, int64_t n, int kb, int B,
                        const void *spl, int cap, int64_t target, int gmax, double penalty,
-                       int *on, double *est, cudaStream_t s) {
+                       int *on, double *est, const int *en, cudaStream_t s) {
   if (kb == 4)
     lrn_decide_kernel<uint32_t><<<1, 512, 0, s>>>(sorted, m, n, 32, B, (const uint32_t *)spl,
-                                                  cap, target, gmax, penalty, on, est);
+                                                  cap, target, gmax, penalty, on, est, en);
   else
     lrn_decide_kernel<uint64_t><<<1, 512, 0, s>>>(sorted, m, n, 64, B, (const uint64_t *)spl,
-                                                  cap, target, gmax, penalty, on, est);
+                                                  cap, target, gmax, penalty, on, est, en);
+  return cudaGetLastError();
+}
+
+cudaError_t lrn_quantiles(const uint64_t *sorted, int64_t m, int kb, int B, void *spl,
+                          cudaStream_t s) {
+  if (kb == 4)
+    lrn_quantile_kernel<uint32_t><<<grid_for(B, 256), 256, 0, s>>>(sorted, m, B, (uint32_t *)spl);
+  else
+    lrn_quantile_kernel<uint64_t><<<grid_for(B, 256), 256, 0, s>>>(sorted, m, B, (uint64_t *)spl);
   return cudaGetLastError();
 }
 

@@ -268,11 +268,14 @@ __device__ __forceinline__ int levels_below(double s, double cap, double target,
 // base-case capacity is distributed once, and the other children of each
 // step cost the levels the digit-width rule gives their mean size.  One CTA,
 // a thread per zone; writes the decision and both estimates (per record).
+// en (optional): a decision already taken; when it kept the digit zones
+// (*en == 0) this one is skipped and both stay.
 template <typename K>
 __global__ void __launch_bounds__(512) lrn_decide_kernel(
     const uint64_t *__restrict__ sorted, int64_t m, int64_t n, int key_bits, int B,
     const K *__restrict__ spl, int cap, int64_t target, int gmax, double penalty, int *on,
-    double *est) {
+    double *est, const int *en) {
+  if (en && !*en) return;
   __shared__ double red[2][32];
   const uint64_t mask = key_bits >= 64 ? ~0ull : ((1ull << key_bits) - 1ull);
   const uint64_t rmax = sorted[m - 1] & mask;
@@ -352,6 +355,17 @@ __global__ void __launch_bounds__(512) lrn_decide_kernel(
     est[0] = cd / (double)n;
     est[1] = cl / (double)n;
   }
+}
+
+// Zone lower bounds at the sample's quantiles: spl[z] = the sorted sample's
+// key of rank z m / B (spl[0] = 0).  These are the zones a perfect CDF model
+// would give; the decision taken on them before any training bounds what the
+// trained model can gain.
+template <typename K>
+__global__ void __launch_bounds__(256) lrn_quantile_kernel(const uint64_t *__restrict__ sorted,
+                                                           int64_t m, int B, K *spl) {
+  for (int z = blockIdx.x * 256 + threadIdx.x; z < B; z += gridDim.x * 256)
+    spl[z] = z ? (K)sorted[(int64_t)z * m / B] : (K)0;
 }
 
 }  // namespace dts

@@ -891,6 +891,8 @@ __device__ void phase_scatter(const Params &P, int level, unsigned char *smem) {
           if constexpr (HV) prefetch_l2<K>(vsrc, tbase, 2 * TILE, P.n);
         } else if constexpr (HV) {
           prefetch_l2<K>(vsrc, tbase, TILE, P.n);
+          // one CTA per SM: nothing else hides the next tile's key loads
+          if (NTS > NT) prefetch_l2<K>(src, tbase + TILE, TILE, P.n);
         } else {
           prefetch_l2<K>(src, tbase + TILE, TILE, P.n);
         }
