@@ -675,16 +675,16 @@ __device__ __forceinline__ void load_tables(const Params &P, int seg, int level,
   }
   __syncthreads();
   const int nz = (T.info.learned ? (1 << T.info.gamma) : (1 << (T.info.t - T.info.lo))) + 1;
-  for (int i = threadIdx.x; i < nz; i += NT) lid_s[i] = __ldcg(P.lid + T.info.zoff + i);
+  for (int i = threadIdx.x; i < nz; i += (int)blockDim.x) lid_s[i] = __ldcg(P.lid + T.info.zoff + i);
   if (T.info.learned && spl_s) {
     const K *spl = (const K *)P.lrn_spl;
-    for (int i = threadIdx.x; i < P.lrn_B; i += NT) spl_s[i] = ld_key<K>(spl + i);
-    for (int i = threadIdx.x; i <= LRN_TAB_N; i += NT) tab_s[i] = __ldcg(P.lrn_tab + i);
+    for (int i = threadIdx.x; i < P.lrn_B; i += (int)blockDim.x) spl_s[i] = ld_key<K>(spl + i);
+    for (int i = threadIdx.x; i <= LRN_TAB_N; i += (int)blockDim.x) tab_s[i] = __ldcg(P.lrn_tab + i);
   }
   if (T.info.hbits) {
     const int cap = 1 << T.info.hbits;
     const K *hk = (const K *)P.hash_keys + T.info.hashoff;
-    for (int i = threadIdx.x; i < cap; i += NT) {
+    for (int i = threadIdx.x; i < cap; i += (int)blockDim.x) {
       hk_s[i] = ld_key<K>(hk + i);
       hid_s[i] = __ldcg(P.hash_ids + T.info.hashoff + i);
     }
