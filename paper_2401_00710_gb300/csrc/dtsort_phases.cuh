@@ -810,11 +810,10 @@ __device__ void phase_scatter(const Params &P, int level, unsigned char *smem) {
   uint16_t *hid_s = cv.take<uint16_t>(HASH_HW);
   unsigned *wc2 = cv.take<unsigned>(NWS * NB_PAIR);  // warp counters, 16-bit pairs
   // FOLD: the warps' counters become their first slots per bucket (tile
-  // offset included), so staging reads one table instead of two; not for
-  // 32-bit key/value pairs, whose scatter spills more with it (measured at
-  // 10^9 records: scatters 15.5 -> 15.7 ms there, 9.0 -> 8.6 ms for 32-bit
-  // keys alone, 12.6 -> 12.4 ms for 64-bit keys)
-  constexpr bool FOLD = !(sizeof(K) == 4 && HV);
+  // offset included), so staging reads one table instead of two (32-bit
+  // key/value pairs with 1024-thread CTAs, 10^9 records: scatters 13.31 ->
+  // 12.93 ms; with the earlier 512-thread CTAs it had lost to spills)
+  constexpr bool FOLD = true;
   unsigned *toff = cv.take<unsigned>(FOLD ? 1 : NB_PAD);
   unsigned *gbase = cv.take<unsigned>(NB_PAD);
   unsigned *base = cv.take<unsigned>(NB_PAD);
