@@ -138,7 +138,14 @@ typedef struct {
                                 4K 64-bit keys each); 1..8, default 8 */
   int32_t merge;             /* dtsort_merge: how each heavy zone's runs are
                                 merged (default DOVETAIL) */
-  int32_t reserved[3];
+  int32_t heavy_min_share;   /* heavy keys are kept for a subproblem only when
+                                they hold at least this many thousandths of its
+                                sample (default 250; -1: any share).  Below
+                                it the subproblem is distributed by its digit
+                                alone, and deeper levels, where those keys
+                                hold more of their smaller subproblems,
+                                detect them */
+  int32_t reserved[2];
 } dtsort_options;
 
 /* Statistics of the last completed sort on this handle (read after sync). */
@@ -180,6 +187,10 @@ typedef struct {
   double learned_estimate[2];     /* LEARNED: estimated record-passes below
                                      level 0 with digit zones, and with learned
                                      zones plus their extra cost */
+  int64_t merge_free_zones;       /* MSD zones with heavy keys whose runs were
+                                     already in key order (heavy keys below and
+                                     above all of the zone's light keys): no
+                                     merge */
 } dtsort_stats;
 
 DTSORT_API const char *dtsort_status_string(dtsort_status s);

@@ -70,7 +70,8 @@ class dtsort_options(ctypes.Structure):
                 ("launch_mode", ctypes.c_int32),
                 ("block_tiles", ctypes.c_int32),
                 ("merge", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 3)]
+                ("heavy_min_share", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2)]
 
 
 class dtsort_stats(ctypes.Structure):
@@ -96,7 +97,8 @@ class dtsort_stats(ctypes.Structure):
                 ("finisher_lsd_tasks", ctypes.c_int64),
                 ("kernel_launches", ctypes.c_int64),
                 ("learned_zones_used", ctypes.c_int64),
-                ("learned_estimate", ctypes.c_double * 2)]
+                ("learned_estimate", ctypes.c_double * 2),
+                ("merge_free_zones", ctypes.c_int64)]
 
     def as_dict(self):
         out = {}

@@ -39,7 +39,8 @@ struct Layout {
 };
 
 struct Opts {
-  int gamma_max, cap, heavy_on, merge_generic, sample_factor, debug_fault, blk_tiles;
+  int gamma_max, cap, heavy_on, heavy_min_share, merge_generic, sample_factor, debug_fault,
+      blk_tiles;
   uint64_t seed;
   unsigned long long wait_ns;
 };
@@ -87,6 +88,8 @@ Opts effective(const dtsort_options &o, const KernelShape &ks, int64_t nsegs = 1
   r.cap = (o.finisher_capacity > 0 && o.finisher_capacity < ks.fin_cap) ? o.finisher_capacity
                                                                         : ks.fin_cap;
   r.heavy_on = o.heavy_detection >= 0 ? 1 : 0;
+  r.heavy_min_share = o.heavy_min_share == 0 ? dts::HEAVY_MIN_SHARE
+                                             : (o.heavy_min_share < 0 ? 0 : o.heavy_min_share);
   r.merge_generic = o.merge == DTSORT_MERGE_GENERIC ? 1 : 0;
   r.sample_factor = o.sample_log_factor > 0 ? o.sample_log_factor : 1;
   r.seed = o.seed ? o.seed : 1;
@@ -381,6 +384,7 @@ dtsort_status run_sort(dtsort_handle h, int op, void *keys, void *vals, const in
   P.gamma_max = std::min(o.gamma_max, dts::GAMMA_HW);
   P.cap = L.cap;
   P.heavy_on = o.heavy_on;
+  P.heavy_min_share = o.heavy_min_share;
   P.merge_generic = o.merge_generic;
   P.target = L.target;
   P.seed = o.seed;
@@ -593,7 +597,8 @@ dtsort_status dtsort_set_options(dtsort_handle h, const dtsort_options *opt) {
       opt->learned_segments < 0 || opt->learned_train_steps < 0 || opt->wait_limit_ms < 0 ||
       opt->debug_fault < 0 || opt->debug_fault > 1 || opt->launch_mode < 0 ||
       opt->launch_mode > 2 || opt->block_tiles < 0 || opt->block_tiles > 8 ||
-      (opt->merge != DTSORT_MERGE_DOVETAIL && opt->merge != DTSORT_MERGE_GENERIC))
+      (opt->merge != DTSORT_MERGE_DOVETAIL && opt->merge != DTSORT_MERGE_GENERIC) ||
+      opt->heavy_min_share < -1 || opt->heavy_min_share > 1000)
     return DTSORT_ERR_INVALID_ARG;
   h->opt = *opt;
   return DTSORT_OK;
@@ -744,6 +749,7 @@ dtsort_status dtsort_get_stats(dtsort_handle h, dtsort_stats *out) {
   out->learned_zones_used = d.learned_used;
   out->learned_estimate[0] = d.learned_est[0];
   out->learned_estimate[1] = d.learned_est[1];
+  out->merge_free_zones = d.free_zones;
   out->check_site = d.check_site;
   out->check_values[0] = d.check_values[0];
   out->check_values[1] = d.check_values[1];

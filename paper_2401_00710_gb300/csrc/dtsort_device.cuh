@@ -30,6 +30,7 @@ constexpr int NT = 512;                       // threads per CTA, every phase
 constexpr int NWARP = NT / 32;
 constexpr int GAMMA_HW = 9;                   // widest digit of one level
 constexpr int HEAVY_HW = 128;                 // heavy keys kept per subproblem
+constexpr int HEAVY_MIN_SHARE = 250;          // default: 1/4 of the sample
 constexpr int NB_HW = (1 << GAMMA_HW) + HEAVY_HW + 1;  // 641
 constexpr int NB_PAD = 648;                   // NB_HW + dummy bucket, padded
 constexpr int NB_PAIR = NB_PAD / 2;           // 16-bit warp counters, two per word
@@ -95,12 +96,15 @@ static_assert(sizeof(Task) == 32, "a task descriptor is two 16-byte copies");
 
 // An MSD zone with heavy buckets, merged after its light bucket is sorted.
 struct MZone {
-  int64_t zs, b0, ze;   // zone [zs, ze); light bucket [zs, zs+b0)
+  int64_t zs, b0, ze;   // zone [zs, ze); light bucket of b0 records
   int64_t mh;           // its heavy keys / sizes / final starts in the store
   int64_t chunk0;       // first merge work item
   int32_t m;            // heavy buckets
   uint8_t obuf;         // output buffer; inputs are in the other one
-  uint8_t pad[3];
+  uint8_t np;           // heavy runs stored before the light bucket (the
+                        // rest after it): the input is [np heavy runs]
+                        // [light bucket][m - np heavy runs]
+  uint8_t pad[2];
 };
 
 struct Ctl {
@@ -120,7 +124,7 @@ struct Ctl {
       st_heavy_records[16], st_overflow[16];
   long long st_fin_lsd_tasks;
   long long st_fin_tasks, st_fin_records, st_copy_records, st_merge_zones,
-      st_merge_records, st_fix_records, st_fix_steps;
+      st_merge_records, st_fix_records, st_fix_steps, st_free_zones;
   // first failed self-check: site, level, and two values
   long long dbg[4];
   // level-0 light bucket sizes of the first subproblem (imbalance statistics)
@@ -145,6 +149,7 @@ struct DevStats {
   int64_t fin_lsd_tasks;
   int64_t learned_used;
   double learned_est[2];
+  int64_t free_zones;
 };
 
 struct Params {
@@ -157,6 +162,8 @@ struct Params {
   int32_t gamma_max;
   int32_t cap;            // largest base-case bucket
   int32_t heavy_on;
+  int32_t heavy_min_share;  // thousandths of a subproblem's sample its heavy
+                            // keys must hold to be kept (0: any)
   int32_t merge_generic;  // 1: merge-path merge of each zone instead of Alg. 3
   int64_t target;         // desired bucket size after distribution
   uint64_t seed;
@@ -606,46 +613,125 @@ __device__ __forceinline__ BucketCtx bucket_ctx(const SegTables<K> &T) {
   return x;
 }
 
-// GetBucketId (Alg. 2): heavy keys through H, overflow past the sampled key
-// range, light keys through L by their MSD zone (or learned zone).
-// lid/hk/hid/spl/tab: the tables in shared memory.
+// Entry z of a subproblem's light table L (Alg. 2), one 32-bit word: the
+// light bucket id of zone z (bits 0-9), the index in the subproblem's sorted
+// heavy list of the zone's first heavy key (bits 10-17), the zone's number of
+// heavy keys (bits 18-25), and LE_MERGE (bit 30): the zone's runs need the
+// dovetail merge.  A zone's buckets are numbered in key order as
+// [heavy keys below its light keys][light bucket][the other heavy keys]: the
+// zone's first bucket is z + (first heavy index), its light bucket id minus
+// that is the number of heavy buckets placed before the light one.
+constexpr int LE_HF = 10, LE_MZ = 18;
+constexpr int32_t LE_ID = (1 << LE_HF) - 1, LE_MERGE = 1 << 30;
+static_assert(NB_HW <= LE_ID + 1 && HEAVY_HW < 256, "light-table fields fit");
+__host__ __device__ constexpr int32_t le_pack(int light, int hfirst, int mz, bool merge) {
+  return light | (hfirst << LE_HF) | (mz << LE_MZ) | (merge ? LE_MERGE : 0);
+}
+__device__ __forceinline__ int le_light(int32_t e) { return e & LE_ID; }
+__device__ __forceinline__ int le_hfirst(int32_t e) { return (e >> LE_HF) & 255; }
+__device__ __forceinline__ int le_mz(int32_t e) { return (e >> LE_MZ) & 255; }
+
+// Heavy id of key in the hash table H (hk/hid), or HEMPTY.
 template <typename K>
+__device__ __forceinline__ unsigned probe_heavy(const K *hk, const uint16_t *hid, int hbits,
+                                                K key) {
+  const uint32_t cap1 = (1u << hbits) - 1u;
+  uint32_t s = hash_slot<K>(key, hbits);
+  while (true) {
+    const uint16_t id = hid[s];
+    const K k = hk[s];  // both loads of a probe issued together
+    if (id == HEMPTY || k == key) return id;
+    s = (s + 1) & cap1;
+  }
+}
+
+// GetBucketId (Alg. 2): overflow past the sampled key range, heavy keys
+// through H, light keys through L by their MSD zone (or learned zone).  A
+// key is looked up in H only when its zone holds heavy keys and it lies
+// between the zone's smallest and largest heavy key (hl: the subproblem's
+// heavy keys, sorted); overflow keys are never heavy (heavy keys are sample
+// keys, the overflow bucket starts above the largest one).
+// lid/hk/hid/hl/spl/tab: the tables in shared memory.  VERIFY (the
+// histogram): a light key of a zone with heavy keys that lies outside the
+// interval the zone's layout leaves for light keys marks the zone's entry
+// LE_MERGE in lid (the zone needs the dovetail merge).
+template <typename K>
+__device__ __forceinline__ bool light_out_of_place(int32_t e, unsigned z, const K *hl, K key);
+template <typename K, bool VERIFY = false>
 __device__ __forceinline__ unsigned bucket_of(const BucketCtx &X, const int32_t *lid,
-                                              const K *hk, const uint16_t *hid, K key,
-                                              const K *spl = nullptr,
+                                              const K *hk, const uint16_t *hid, const K *hl,
+                                              K key, const K *spl = nullptr,
                                               const float *tab = nullptr,
                                               unsigned *steps = nullptr) {
-  if (X.hbits) {
-    const uint32_t cap1 = (1u << X.hbits) - 1u;
-    uint32_t s = hash_slot<K>(key, X.hbits);
-    while (true) {
-      const uint16_t id = hid[s];
-      const K k = hk[s];  // both loads of a probe issued together
-      if (id == HEMPTY) break;
-      if (k == key) return id;
-      s = (s + 1) & cap1;
-    }
-  }
+  unsigned z;
   if (X.learned) {
+    if (X.hbits) {  // the learned lookup is dearer than a probe: probe first
+      const unsigned id = probe_heavy<K>(hk, hid, X.hbits, key);
+      if (id != HEMPTY) return id;
+    }
     unsigned st;
-    const unsigned z = learned_zone<K>(key, spl, tab, X.B, &st);
+    z = learned_zone<K>(key, spl, tab, X.B, &st);
     if (steps) *steps = st;
-    return (unsigned)lid[z];
+    const int32_t e = lid[z];
+    if constexpr (VERIFY) {
+      if (le_mz(e) && !(e & LE_MERGE) && light_out_of_place<K>(e, z, hl, key))
+        atomicOr(const_cast<int32_t *>(lid) + z, LE_MERGE);
+    }
+    return (unsigned)le_light(e);
   }
   if constexpr (sizeof(K) == 4) {
     const uint32_t m = ((uint32_t)key - (uint32_t)X.base) & (uint32_t)X.hmask;
     if (X.t < 32 && (m >> X.t) != 0) return (unsigned)(X.nb - 1);
-    return (unsigned)lid[m >> X.lo];
+    z = m >> X.lo;
   } else {
     const uint64_t m = ((uint64_t)key - X.base) & X.hmask;
     if (X.t < 64 && (m >> X.t) != 0) return (unsigned)(X.nb - 1);
-    return (unsigned)lid[m >> X.lo];
+    z = (unsigned)(m >> X.lo);
   }
+  const int32_t e = lid[z];
+  if (X.hbits) {
+    const int mz = le_mz(e);
+    if (mz) {
+      // above (below) all of the zone's heavy keys: light, and in place
+      // unless heavy buckets are stored after (before) the light one
+      const int hf = le_hfirst(e);
+      const int mp = le_light(e) - (int)z - hf;
+      const K hmin = hl[hf], hmax = hl[hf + mz - 1];
+      bool out;
+      if (hmax < key) {
+        out = mp < mz;
+      } else if (key < hmin) {
+        out = mp > 0;
+      } else if (key == hmin) {  // the zone's first heavy key: no probe
+        return z + hf + (mp > 0 ? 0 : 1);
+      } else if (key == hmax) {  // and its last
+        return z + hf + mz - 1 + (mz - 1 < mp ? 0 : 1);
+      } else {
+        const unsigned id = probe_heavy<K>(hk, hid, X.hbits, key);
+        if (id != HEMPTY) return id;
+        out = VERIFY && light_out_of_place<K>(e, z, hl, key);
+      }
+      if constexpr (VERIFY) {
+        if (out && !(e & LE_MERGE)) atomicOr(const_cast<int32_t *>(lid) + z, LE_MERGE);
+      }
+    }
+  }
+  return (unsigned)le_light(e);
+}
+
+// Zone z's light-table entry e (zone with heavy keys, not yet marked for a
+// merge) and a light key of it: true when the key lies outside the interval
+// the zone's layout leaves for light keys, i.e. the zone needs the merge.
+template <typename K>
+__device__ __forceinline__ bool light_out_of_place(int32_t e, unsigned z, const K *hl, K key) {
+  const int hf = le_hfirst(e), mz = le_mz(e);
+  const int mp = le_light(e) - (int)z - hf;  // heavy buckets before the light one
+  return (mp > 0 && key < hl[hf + mp - 1]) || (mp < mz && hl[hf + mp] < key);
 }
 
 template <typename K>
 __device__ __forceinline__ void load_tables(const Params &P, int seg, int level, SegTables<K> &T,
-                                            int32_t *lid_s, K *hk_s, uint16_t *hid_s,
+                                            int32_t *lid_s, K *hk_s, uint16_t *hid_s, K *hl_s,
                                             K *spl_s = nullptr, float *tab_s = nullptr) {
   // all threads call; T lives in shared memory
   if (threadIdx.x == 0) {
@@ -675,7 +761,16 @@ __device__ __forceinline__ void load_tables(const Params &P, int seg, int level,
   }
   __syncthreads();
   const int nz = (T.info.learned ? (1 << T.info.gamma) : (1 << (T.info.t - T.info.lo))) + 1;
-  for (int i = threadIdx.x; i < nz; i += (int)blockDim.x) lid_s[i] = __ldcg(P.lid + T.info.zoff + i);
+  for (int i = threadIdx.x; i < nz; i += (int)blockDim.x) {
+    int32_t e = __ldcg(P.lid + T.info.zoff + i);
+    // self-check: the entry's bucket and heavy-list range lie in the tables
+    if (e < 0 || le_light(e) >= T.info.nb || le_hfirst(e) + le_mz(e) > T.info.nheavy ||
+        (le_mz(e) && !T.info.hbits)) {
+      check_failed(P, 9, seg, (long long)e);
+      e = 0;
+    }
+    lid_s[i] = e;
+  }
   if (T.info.learned && spl_s) {
     const K *spl = (const K *)P.lrn_spl;
     for (int i = threadIdx.x; i < P.lrn_B; i += (int)blockDim.x) spl_s[i] = ld_key<K>(spl + i);
@@ -688,6 +783,9 @@ __device__ __forceinline__ void load_tables(const Params &P, int seg, int level,
       hk_s[i] = ld_key<K>(hk + i);
       hid_s[i] = __ldcg(P.hash_ids + T.info.hashoff + i);
     }
+    const int nh = T.info.nheavy < HEAVY_HW ? T.info.nheavy : HEAVY_HW;
+    for (int i = threadIdx.x; i < nh; i += (int)blockDim.x)
+      hl_s[i] = ld_key<K>((const K *)P.heavy + T.info.hoff + i);
   }
   __syncthreads();
 }

@@ -170,6 +170,7 @@ extern "C" dtsort_status dtsort_u32_kv_noalloc(uint32_t *keys, uint32_t *values,
   P.gamma_max = dts::GAMMA_HW;
   P.cap = Sh::FIN_CAP;
   P.heavy_on = 1;
+  P.heavy_min_share = dts::HEAVY_MIN_SHARE;
   P.target = L.target;
   P.seed = 1;
   P.sample_factor = 1;

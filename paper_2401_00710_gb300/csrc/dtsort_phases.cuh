@@ -91,6 +91,7 @@ constexpr size_t scatter_smem() {
   sc += 64 + sizeof(SegTables<K>);
   sc += 16 + 4 * ((1 << GAMMA_HW) + 1);            // lid
   sc += 16 + sizeof(K) * HASH_HW + 16 + 2 * HASH_HW;  // hash
+  sc += 16 + sizeof(K) * HEAVY_HW;                 // heavy keys, sorted
   sc += 16 + 4 * (size_t)NWS * NB_PAIR;            // warp counters
   sc += 3 * (16 + 4 * NB_PAD);                     // tile offsets, bases
   sc += 16 + 4 * (NWS + 1);                        // warp sums
@@ -112,7 +113,7 @@ constexpr size_t smem_bytes() {
   fin += 16 + 4 * (NWARP + 1) + 16 + 4 * NWARP + 4 * 16 + 16 + 16 + 2 * sizeof(Task) + 256;
   // sampler
   size_t smp = 16 + sizeof(K) * SMAX + 16 + sizeof(K) * (SMAX / 2 + 8) + 16 + 4 * 1024 +
-               16 + sizeof(K) * HASH_HW + 16 + 2 * HASH_HW + 512;
+               16 + sizeof(K) * HASH_HW + 16 + 2 * HASH_HW + 6 * (16 + 4 * HEAVY_HW) + 16 + 512;
   size_t m = sc > fin ? sc : fin;
   return m > smp ? m : smp;
 }
@@ -123,11 +124,13 @@ template <typename K, bool HV>
 constexpr size_t phase_smem_bytes(int ph) {
   // histogram: tables + one count row
   const size_t hist = 64 + sizeof(SegTables<K>) + 16 + 4 * ((1 << GAMMA_HW) + 1) + 16 +
-                      sizeof(K) * HASH_HW + 16 + 2 * HASH_HW + 16 + 4 * NB_PAD + 16 +
+                      sizeof(K) * HASH_HW + 16 + 2 * HASH_HW + 16 + sizeof(K) * HEAVY_HW +
+                      16 + 4 * NB_PAD + 16 +
                       sizeof(K) * (1 << GAMMA_HW) + 16 + 4 * (LRN_TAB_N + 1) + 256;
   // sample: the on-chip sample and its tables
   const size_t smp = 16 + sizeof(K) * SMAX + 16 + sizeof(K) * (SMAX / 2 + 8) + 16 + 4 * 1024 +
-                     16 + sizeof(K) * HASH_HW + 16 + 2 * HASH_HW + 512;
+                     16 + sizeof(K) * HASH_HW + 16 + 2 * HASH_HW + 6 * (16 + 4 * HEAVY_HW) +
+                     16 + 512;
   // bucket scan: counts, offsets, light table
   const size_t scan = 16 + 8 * NB_PAD + 16 + 8 * (NB_PAD + 1) + 16 + 4 * ((1 << GAMMA_HW) + 1) +
                       16 + 8 * (NWARP + 1) + 256;
@@ -141,10 +144,11 @@ constexpr size_t phase_smem_bytes(int ph) {
     case 9:                                    // KP_MERGE_PREP
     case 10: {                                 // KP_MERGE: heavy runs, warp sums;
       const size_t dov =                       // or the generic merge's sub-tile
-          3 * (16 + 8 * (HASH_HW / 2 + 1)) + 16 + 8 * (NWARP + 1) + 16 + sizeof(MZone) + 256;
+          3 * (16 + 8 * (HASH_HW / 2 + 1)) + 16 + 8 * (NWARP + 1) + 16 + sizeof(MZone) + 16 + 8 +
+          256;
       const size_t gen = 16 + sizeof(K) * MERGE_SUB + 16 + sizeof(K) * (HV ? MERGE_SUB : 1) +
                          16 + 2 * MERGE_SUB + 16 + 8 * (MERGE_CHUNK / MERGE_SUB + 1) + 16 +
-                         sizeof(MZone) + 256;
+                         sizeof(MZone) + 16 + 8 + 256;
       return dov > gen ? dov : gen;
     }
     case 11: return 256;                       // KP_STATS
@@ -156,11 +160,14 @@ constexpr size_t phase_smem_bytes(int ph) {
 // Threads per CTA of each per-phase kernel.
 __host__ __device__ constexpr int phase_threads(int ph) { return ph == 6 ? SCATTER_NT : NT; }
 
-// CTAs per SM the per-phase kernels are built for: the light phases 3, the
-// base case 2, the scatter 1024 threads' worth (64 registers a thread; their
-// shared memory allows no more).
+// CTAs per SM the per-phase kernels are built for: the sample and the scans
+// 3; the histogram 2 (64 registers: a thread's keys all loaded before the
+// table lookups, no spills; 10^9 u32 key/value pairs, uniform keys: the two
+// histograms 1.52 -> 1.35 ms against 3 CTAs of 40 registers); the base case 2;
+// the scatter 1024 threads' worth (64 registers a thread; their shared memory
+// allows no more).
 __host__ __device__ constexpr int phase_min_blocks(int ph) {
-  return (ph >= 2 && ph <= 5) ? 3 : (ph == 6 ? 1024 / SCATTER_NT : 2);
+  return (ph == 2 || ph == 4 || ph == 5) ? 3 : (ph == 6 ? 1024 / SCATTER_NT : 2);
 }
 
 // ----------------------------------------------------------------- queues
@@ -176,7 +183,15 @@ __device__ __forceinline__ void push_task(const Params &P, const Task &t) {
 __device__ __forceinline__ void push_copy(const Params &P, int64_t start, int64_t size,
                                           int src, int dst) {
   if (size <= 0 || src == dst) return;
-  for (int64_t a = 0; a < size; a += COPY_CHUNK) {
+  // all of the run's tasks reserved at once (a heavy run can be 10^8 records)
+  const long long k = (size + COPY_CHUNK - 1) / COPY_CHUNK;
+  const long long i0 = atomic_add_ll(&P.ctl->ntasks, k);
+  for (long long q = 0; q < k; ++q) {
+    if (i0 + q >= P.tmax) {
+      latch(P, ERR_INTERNAL);
+      return;
+    }
+    const int64_t a = q * COPY_CHUNK;
     Task t;
     t.start = start + a;
     t.size = size - a < COPY_CHUNK ? size - a : COPY_CHUNK;
@@ -185,7 +200,7 @@ __device__ __forceinline__ void push_copy(const Params &P, int64_t start, int64_
     t.src = (uint8_t)src;
     t.dst = (uint8_t)dst;
     t.kind = TASK_COPY;
-    push_task(P, t);
+    P.tasks[i0 + q] = t;
   }
 }
 
@@ -344,6 +359,13 @@ __device__ void phase_sample(const Params &P, int level, unsigned char *smem) {
   uint16_t *hid = cv.take<uint16_t>(HASH_HW);
   long long *sh = cv.take<long long>(NWARP + 1);
   long long *resv = cv.take<long long>(1);
+  // per heavy key: its zone, its first sample index and occurrences, its
+  // zone's sample index range, its class / its zone's layout; and the count
+  // of heavy keys kept
+  int *hzone = cv.take<int>(HEAVY_HW), *hlb = cv.take<int>(HEAVY_HW);
+  int *hocc = cv.take<int>(HEAVY_HW), *hzs = cv.take<int>(HEAVY_HW);
+  int *hze = cv.take<int>(HEAVY_HW), *hcls = cv.take<int>(HEAVY_HW);
+  int *nkeep = cv.take<int>(1);
   for (int64_t si = blockIdx.x; si < nseg; si += gridDim.x) {
     const Seg S = ldcg_obj(&P.segs[p][si]);
     SegInfo I = ldcg_obj(&P.info[si]);
@@ -432,6 +454,102 @@ __device__ void phase_sample(const Params &P, int level, unsigned char *smem) {
       nh = (int)carry;
       if (nh > hcap) nh = hcap;
       if (nh > 0) {
+        // the layout of each zone's buckets (numbered in key order): heavy
+        // keys below every light key of the zone's sample, the light bucket,
+        // the other heavy keys.  A zone whose light keys all fall between
+        // them needs no dovetail merge (checked on every light key by the
+        // histogram).  Heavy keys with sampled light keys on both sides
+        // ("interior") force the merge of the zone; when they hold less
+        // than 1/8 of the rest of the zone's sample they are dropped
+        // instead (their records stay light and are distributed once more).
+        __syncthreads();  // hv, written after the last scan's barrier
+        for (int j = threadIdx.x; j < nh; j += NT) {
+          const K h = hv[j];
+          const int zj = (int)zone_of(h);
+          int a = 0, b = (int)m;
+          while (a < b) {
+            const int mid = (a + b) >> 1;
+            if (Ssm[mid] < h) a = mid + 1;
+            else b = mid;
+          }
+          const int lbj = a;
+          b = (int)m;
+          while (a < b) {
+            const int mid = (a + b) >> 1;
+            if (!(h < Ssm[mid])) a = mid + 1;
+            else b = mid;
+          }
+          const int ubj = a;
+          a = 0;
+          b = lbj;
+          while (a < b) {
+            const int mid = (a + b) >> 1;
+            if (zone_of(Ssm[mid]) < (uint64_t)zj) a = mid + 1;
+            else b = mid;
+          }
+          const int zsj = a;
+          a = ubj;
+          b = (int)m;
+          while (a < b) {
+            const int mid = (a + b) >> 1;
+            if (zone_of(Ssm[mid]) <= (uint64_t)zj) a = mid + 1;
+            else b = mid;
+          }
+          hzone[j] = zj;
+          hlb[j] = lbj;
+          hocc[j] = ubj - lbj;
+          hzs[j] = zsj;
+          hze[j] = a;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+          // classes: 0 below the zone's light sample keys, 1 above, 2 interior
+          int kept = 0;
+          long long wkept = 0;  // sample keys equal to a kept heavy key
+          for (int j0 = 0; j0 < nh;) {
+            int j1 = j0 + 1;
+            while (j1 < nh && hzone[j1] == hzone[j0]) ++j1;
+            int occ = 0;
+            for (int j = j0; j < j1; ++j) occ += hocc[j];
+            int below = 0, npre = 0, nint = 0, wint = 0;
+            for (int j = j0; j < j1; ++j) {
+              const int lbelow = (hlb[j] - hzs[j0]) - below;
+              const int labove = (hze[j0] - hlb[j] - hocc[j]) - (occ - below - hocc[j]);
+              const int cl = lbelow == 0 ? 0 : (labove == 0 ? 1 : 2);
+              hcls[j] = cl;
+              npre += cl == 0;
+              if (cl == 2) {
+                ++nint;
+                wint += hocc[j];
+              }
+              below += hocc[j];
+            }
+            const int wrest = (hze[j0] - hzs[j0]) - wint;
+            const bool drop = nint > 0 && 8 * wint < wrest;
+            const bool force = nint > 0 && !drop;
+            // layout code per kept key: heavy buckets before the light one
+            // (bits 0-7), forced merge (bit 8)
+            const int code = (force ? 0 : npre) | (force ? 256 : 0);
+            for (int j = j0; j < j1; ++j) {
+              if (drop && hcls[j] == 2) continue;
+              wkept += hocc[j];
+              hv[kept] = hv[j];
+              hzone[kept] = hzone[j];
+              hcls[kept] = code;
+              ++kept;
+            }
+            j0 = j1;
+          }
+          // heavy keys that hold less than the minimum share of the sample
+          // are not worth the table lookup every record of the subproblem
+          // then pays: the digit alone distributes it
+          if (1000 * wkept < (long long)P.heavy_min_share * m) kept = 0;
+          *nkeep = kept;
+        }
+        __syncthreads();
+        nh = *nkeep;
+      }
+      if (nh > 0) {
         // room for this subproblem's heavy buckets in the merge store
         if (threadIdx.x == 0) {
           const long long off = atomic_add_ll(&c->mh_alloc, (long long)nh);
@@ -444,18 +562,27 @@ __device__ void phase_sample(const Params &P, int level, unsigned char *smem) {
         else I.mhoff = off;
       }
     }
-    // heavy list out; light table L[z] = z + #heavy keys in zones < z
+    // heavy list out; light table: zone z's buckets start at z + (heavy keys
+    // in zones < z), its light bucket after the heavy keys placed before it
     for (int j = threadIdx.x; j < nh; j += NT) ((K *)P.heavy)[I.hoff + j] = hv[j];
     const int nz = 1 << geff;
     for (int z = threadIdx.x; z <= nz; z += NT) {
       int a = 0, b = nh;
       while (a < b) {
         const int mid = (a + b) >> 1;
-        const uint64_t zm = zone_of(hv[mid]);
-        if (zm < (uint64_t)z) a = mid + 1;
+        if (hzone[mid] < z) a = mid + 1;
         else b = mid;
       }
-      P.lid[I.zoff + z] = z + a;
+      int e = a;
+      b = nh;
+      while (e < b) {
+        const int mid = (e + b) >> 1;
+        if (hzone[mid] <= z) e = mid + 1;
+        else b = mid;
+      }
+      const int mz = e - a;
+      const int code = mz ? hcls[a] : 0;
+      P.lid[I.zoff + z] = le_pack(z + a + (code & 255), a, mz, (code & 256) != 0);
     }
     int hbits = 0;
     if (nh > 0) {
@@ -465,13 +592,18 @@ __device__ void phase_sample(const Params &P, int level, unsigned char *smem) {
       for (int i = threadIdx.x; i < cap; i += NT) hid[i] = HEMPTY;
       __syncthreads();
       if (threadIdx.x == 0) {
+        int g0 = 0;  // first heavy key of the current zone
         for (int j = 0; j < nh; ++j) {
           const K key = hv[j];
-          const int zone = (int)zone_of(key);
+          const int zone = hzone[j];
+          if (j == 0 || zone != hzone[j - 1]) g0 = j;
+          // bucket of the zone's (j - g0)-th heavy key: after the light
+          // bucket unless among the ones placed before it
+          const int id = zone + j + (j - g0 < (hcls[j] & 255) ? 0 : 1);
           uint32_t s = hash_slot<K>(key, hbits);
           while (hid[s] != HEMPTY) s = (s + 1) & (uint32_t)(cap - 1);
           hk[s] = key;
-          hid[s] = (uint16_t)(zone + j + 1);
+          hid[s] = (uint16_t)id;
         }
       }
       __syncthreads();
@@ -511,6 +643,7 @@ __device__ void phase_hist(const Params &P, int level, unsigned char *smem) {
   int32_t *lid_s = cv.take<int32_t>((1 << GAMMA_HW) + 1);
   K *hk_s = cv.take<K>(HASH_HW);
   uint16_t *hid_s = cv.take<uint16_t>(HASH_HW);
+  K *hl_s = cv.take<K>(HEAVY_HW);
   unsigned *cnt = cv.take<unsigned>(NB_PAD);
   K *spl_s = cv.take<K>(1 << GAMMA_HW);
   float *tab_s = cv.take<float>(LRN_TAB_N + 1);
@@ -527,13 +660,14 @@ __device__ void phase_hist(const Params &P, int level, unsigned char *smem) {
     if (cur < 0 || r >= cur_end) {
       const int s = find_blk_seg(P, nseg, r);
       if (s != cur) {
-        load_tables<K>(P, s, level, T, lid_s, hk_s, hid_s, spl_s, tab_s);
+        load_tables<K>(P, s, level, T, lid_s, hk_s, hid_s, hl_s, spl_s, tab_s);
         cur = s;
       }
       cur_end = T.info.blk0 + T.info.nblk;
     }
     const int nb = T.info.nb;
     const int lo = T.info.lo;
+
     const unsigned gmask = (1u << (T.info.t - T.info.lo)) - 1u;
     const bool fast = T.info.hbits == 0 && T.info.t >= T.hi && !T.info.learned;
     const uint64_t kbase = T.base;
@@ -553,40 +687,56 @@ __device__ void phase_hist(const Params &P, int level, unsigned char *smem) {
       const int tn = brem - tb < S::TILE ? (int)(brem - tb) : S::TILE;
       const K *ts = src + b0 + tb;
       if (threadIdx.x == 0) prefetch_l2<K>(src, b0 + tb + S::TILE, S::TILE, P.n);
-      K key[S::ITEMS];
-#pragma unroll
-      for (int j = 0; j < S::ITEMS; ++j) {
-        const int i = w * 32 * S::ITEMS + j * 32 + lane;
-        key[j] = i < tn ? ld_key<K>(ts + i) : (K)0;
-      }
       if (fast) {
+        // all of a thread's keys loaded before any is counted
+        K key[S::ITEMS];
+#pragma unroll
+        for (int j = 0; j < S::ITEMS; ++j) {
+          const int i = w * 32 * S::ITEMS + j * 32 + lane;
+          key[j] = i < tn ? ld_key<K>(ts + i) : (K)0;
+        }
 #pragma unroll
         for (int j = 0; j < S::ITEMS; ++j) {
           const int i = w * 32 * S::ITEMS + j * 32 + lane;
           // b <= gmask < nb: the tables were checked when loaded
           if (i < tn) atomicAdd(&cnt[fast_digit<K>(key[j], kbase, lo, gmask)], 1u);
         }
-      } else if (X.learned) {
-#pragma unroll
-        for (int j = 0; j < S::ITEMS; ++j) {
-          const int i = w * 32 * S::ITEMS + j * 32 + lane;
-          if (i < tn) {
-            unsigned st = 0;
-            const unsigned b = bucket_of<K>(X, lid_s, hk_s, hid_s, key[j], spl_s, tab_s, &st);
-            if (b < (unsigned)nb) atomicAdd(&cnt[b], 1u);
-            else bad = b;
-            fix_recs += st != 0;
-            fix_steps += st;
-          }
-        }
       } else {
+        // all of a thread's keys loaded before any is looked up
+        constexpr int HC = S::ITEMS;
+        static_assert(S::ITEMS % HC == 0, "whole key groups");
 #pragma unroll
-        for (int j = 0; j < S::ITEMS; ++j) {
-          const int i = w * 32 * S::ITEMS + j * 32 + lane;
-          if (i < tn) {
-            const unsigned b = bucket_of<K>(X, lid_s, hk_s, hid_s, key[j]);
-            if (b < (unsigned)nb) atomicAdd(&cnt[b], 1u);
-            else bad = b;
+        for (int j0 = 0; j0 < S::ITEMS; j0 += HC) {
+          K key[HC];
+#pragma unroll
+          for (int r = 0; r < HC; ++r) {
+            const int i = w * 32 * S::ITEMS + (j0 + r) * 32 + lane;
+            key[r] = i < tn ? ld_key<K>(ts + i) : (K)0;
+          }
+          if (X.learned) {
+#pragma unroll
+            for (int r = 0; r < HC; ++r) {
+              const int i = w * 32 * S::ITEMS + (j0 + r) * 32 + lane;
+              if (i < tn) {
+                unsigned st = 0;
+                const unsigned b = bucket_of<K, true>(X, lid_s, hk_s, hid_s, hl_s, key[r],
+                                                      spl_s, tab_s, &st);
+                if (b < (unsigned)nb) atomicAdd(&cnt[b], 1u);
+                else bad = b;
+                fix_recs += st != 0;
+                fix_steps += st;
+              }
+            }
+          } else {
+#pragma unroll
+            for (int r = 0; r < HC; ++r) {
+              const int i = w * 32 * S::ITEMS + (j0 + r) * 32 + lane;
+              if (i < tn) {
+                const unsigned b = bucket_of<K, true>(X, lid_s, hk_s, hid_s, hl_s, key[r]);
+                if (b < (unsigned)nb) atomicAdd(&cnt[b], 1u);
+                else bad = b;
+              }
+            }
           }
         }
       }
@@ -594,6 +744,16 @@ __device__ void phase_hist(const Params &P, int level, unsigned char *smem) {
     __syncthreads();
     unsigned *row = P.cmat + T.info.coff + lr * nb;
     for (int b = threadIdx.x; b < nb; b += NT) row[b] = cnt[b];
+    // zones whose layout a light key of this block broke (LE_MERGE in the
+    // on-chip table) are marked in the global light table, which the bucket
+    // scan reads
+    if (T.info.hbits) {
+      const int nzl = T.info.learned ? (1 << T.info.gamma) : (1 << (T.info.t - T.info.lo));
+      for (int z = threadIdx.x; z < nzl; z += NT) {
+        const int32_t e = lid_s[z];
+        if ((e & LE_MERGE) && le_mz(e)) atomicOr(P.lid + T.info.zoff + z, LE_MERGE);
+      }
+    }
     __syncthreads();
   }
   if (fix_recs) {
@@ -711,41 +871,61 @@ __device__ void phase_scan(const Params &P, int level, unsigned char *smem) {
     for (int b = threadIdx.x; b < nb; b += NT) P.bstart[I.boff + b] = S.start + excl[b];
     const int res = S.res;
     long long heavy_recs = 0;
+    long long free_zones = 0;
     for (int z = threadIdx.x; z < nz; z += NT) {
-      const int lb = lid_s[z], le = lid_s[z + 1];
-      if (lb < 0 || le <= lb || le > nb - 1) {
-        check_failed(P, 7, z, (long long)lb * 65536 + le);
+      // zone z's buckets [zb, zb + m], its light bucket lb among them (mp
+      // heavy buckets before it)
+      const int32_t e = lid_s[z];
+      const int lb = le_light(e), hf = le_hfirst(e), m = le_mz(e);
+      const int zb = z + hf, mp = lb - zb;
+      if (e < 0 || mp < 0 || mp > m || zb + m >= nb - 1 || hf + m > I.nheavy) {
+        check_failed(P, 7, z, (long long)e);
         continue;
       }
-      const int m = le - lb - 1;
-      const int64_t zs = S.start + excl[lb];
+      const int64_t zs = S.start + excl[zb];
+      const int64_t ls = S.start + excl[lb];
       const int64_t b0 = cntv[lb];
-      const int64_t ze = S.start + excl[le];
+      const int64_t ze = S.start + excl[zb + m + 1];
       int light_res = res;
       if (m > 0) {
-        light_res = res ^ 1;  // the merge reads from the other buffer
-        const int64_t nch = (ze - zs + MERGE_CHUNK - 1) / MERGE_CHUNK;
-        const unsigned long long old =
-            atomicAdd(&c->zone_alloc, (1ull << 40) | (unsigned long long)nch);
-        const int64_t zidx = (int64_t)(old >> 40);
-        const int64_t mh = I.mhoff + (lb - z);
-        for (int q = 0; q < m; ++q) {
-          ((K *)P.mh_keys)[mh + q] = ld_key<K>((const K *)P.heavy + I.hoff + (lb - z) + q);
-          P.mh_sizes[mh + q] = cntv[lb + 1 + q];
-        }
-        MZone Z;
-        Z.zs = zs;
-        Z.b0 = b0;
-        Z.ze = ze;
-        Z.mh = mh;
-        Z.chunk0 = (int64_t)(old & ((1ull << 40) - 1));
-        Z.m = m;
-        Z.obuf = (uint8_t)res;
-        if (zidx < P.mhmax) P.zones[zidx] = Z;
-        else latch(P, ERR_INTERNAL);
         heavy_recs += ze - zs - b0;
-        // heavy runs must sit in the merge's input buffer
-        if (dstb == res) push_copy(P, zs + b0, ze - zs - b0, dstb, dstb ^ 1);
+        // the heavy runs: [zs, ls) before the light bucket, [ls + b0, ze) after
+        if ((e & LE_MERGE) && b0 > 0) {
+          light_res = res ^ 1;  // the merge reads from the other buffer
+          const int64_t nch = (ze - zs + MERGE_CHUNK - 1) / MERGE_CHUNK;
+          const unsigned long long old =
+              atomicAdd(&c->zone_alloc, (1ull << 40) | (unsigned long long)nch);
+          const int64_t zidx = (int64_t)(old >> 40);
+          const int64_t mh = I.mhoff + hf;
+          for (int q = 0; q < m; ++q) {
+            ((K *)P.mh_keys)[mh + q] = ld_key<K>((const K *)P.heavy + I.hoff + hf + q);
+            P.mh_sizes[mh + q] = cntv[zb + q + (q < mp ? 0 : 1)];
+          }
+          MZone Z;
+          Z.zs = zs;
+          Z.b0 = b0;
+          Z.ze = ze;
+          Z.mh = mh;
+          Z.chunk0 = (int64_t)(old & ((1ull << 40) - 1));
+          Z.m = m;
+          Z.obuf = (uint8_t)res;
+          Z.np = (uint8_t)mp;
+          if (zidx < P.mhmax) P.zones[zidx] = Z;
+          else latch(P, ERR_INTERNAL);
+          // heavy runs must sit in the merge's input buffer
+          if (dstb == res) {
+            push_copy(P, zs, ls - zs, dstb, dstb ^ 1);
+            push_copy(P, ls + b0, ze - ls - b0, dstb, dstb ^ 1);
+          }
+        } else {
+          // the zone's runs are already in key order: the light bucket's
+          // result and the heavy runs go straight to the required buffer
+          free_zones += 1;
+          if (dstb != res) {
+            push_copy(P, zs, ls - zs, dstb, res);
+            push_copy(P, ls + b0, ze - ls - b0, dstb, res);
+          }
+        }
       }
       // the light bucket's keys: digit zone z covers base + [z, z+1) * 2^lo;
       // learned zone z covers [spl[z], spl[z+1])
@@ -759,7 +939,7 @@ __device__ void phase_scan(const Params &P, int level, unsigned char *smem) {
         cbase = a;
         chi = top >= a ? bitlen64(top - a) : 0;
       }
-      emit_child(P, p ^ 1, zs, b0, chi, cbase, dstb, light_res, S.ntotal);
+      emit_child(P, p ^ 1, ls, b0, chi, cbase, dstb, light_res, S.ntotal);
       if (level == 0 && si == 0) {
         atomicAdd(&c->st_bsum, (double)b0);
         atomicAdd(&c->st_bsq, (double)b0 * (double)b0);
@@ -776,6 +956,7 @@ __device__ void phase_scan(const Params &P, int level, unsigned char *smem) {
       }
     }
     if (heavy_recs) atomic_add_ll(&c->st_heavy_records[level < 15 ? level : 15], heavy_recs);
+    if (free_zones) atomic_add_ll(&c->st_free_zones, free_zones);
     __syncthreads();
   }
 }
@@ -808,6 +989,7 @@ __device__ void phase_scatter(const Params &P, int level, unsigned char *smem) {
   int32_t *lid_s = cv.take<int32_t>((1 << GAMMA_HW) + 1);
   K *hk_s = cv.take<K>(HASH_HW);
   uint16_t *hid_s = cv.take<uint16_t>(HASH_HW);
+  K *hl_s = cv.take<K>(HEAVY_HW);
   unsigned *wc2 = cv.take<unsigned>(NWS * NB_PAIR);  // warp counters, 16-bit pairs
   // FOLD: the warps' counters become their first slots per bucket (tile
   // offset included), so staging reads one table instead of two (32-bit
@@ -845,7 +1027,7 @@ __device__ void phase_scatter(const Params &P, int level, unsigned char *smem) {
     if (cur < 0 || r >= cur_end) {
       const int s = find_blk_seg(P, nseg, r);
       if (s != cur) {
-        load_tables<K>(P, s, level, T, lid_s, hk_s, hid_s, spl_s, tab_s);
+        load_tables<K>(P, s, level, T, lid_s, hk_s, hid_s, hl_s, spl_s, tab_s);
         cur = s;
       }
       cur_end = T.info.blk0 + T.info.nblk;
@@ -913,7 +1095,8 @@ __device__ void phase_scatter(const Params &P, int level, unsigned char *smem) {
         for (int j = 0; j < S::ITEMS; ++j) {
           const int i = w * 32 * S::ITEMS + j * 32 + lane;
           const unsigned b =
-              i < tn ? bucket_of<K>(X, lid_s, hk_s, hid_s, key[j], spl_s, tab_s) : (unsigned)nb;
+              i < tn ? bucket_of<K>(X, lid_s, hk_s, hid_s, hl_s, key[j], spl_s, tab_s)
+                     : (unsigned)nb;
           br[j] = (b << 16) | warp_rank(b, myslot, mywc);
         }
       }
@@ -1262,6 +1445,31 @@ __device__ __forceinline__ bool fin_core(const K (&rk)[Shape<K, HV>::FIN_IT], in
   return true;
 }
 
+// n elements s -> d by the CTA, CB per thread at a time with all their loads
+// issued before the stores.  (16-byte vectors cost the base case's kernel
+// spills through the call.)
+template <typename K>
+__device__ __forceinline__ void copy_elems(const K *s, K *d, int64_t n) {
+  constexpr int CB = 8;
+  for (int64_t b = threadIdx.x; b < n; b += (int64_t)CB * NT) {
+    K r[CB];
+#pragma unroll
+    for (int q = 0; q < CB; ++q)
+      if (b + (int64_t)q * NT < n) r[q] = ld_key<K>(s + b + (int64_t)q * NT);
+#pragma unroll
+    for (int q = 0; q < CB; ++q)
+      if (b + (int64_t)q * NT < n) d[b + (int64_t)q * NT] = r[q];
+  }
+}
+
+// A plain copy of n records by the CTA (keys, then values).  Not inlined: its
+// registers do not add to the base case's.
+template <typename K, bool HV>
+__device__ __noinline__ void copy_run(const K *ks, K *kd, const K *vs, K *vd, int64_t n) {
+  copy_elems<K>(ks, kd, n);
+  if constexpr (HV) copy_elems<K>(vs, vd, n);
+}
+
 template <typename K, bool HV>
 __device__ void phase_finish(const Params &P, int level, unsigned char *smem) {
   using S = Shape<K, HV>;
@@ -1371,9 +1579,14 @@ __device__ void phase_finish(const Params &P, int level, unsigned char *smem) {
         if (!ok) check_failed(P, 6, ti, tk.size);
       }
       if (ok) {
-        for (int64_t i = threadIdx.x; i < tk.size; i += NT) {
-          kdst[tk.start + i] = ld_key<K>(ksrc + tk.start + i);
-          if constexpr (HV) vdst[tk.start + i] = ld_key<K>(vsrc + tk.start + i);
+        if constexpr (sizeof(K) == 4) {
+          copy_run<K, HV>(ksrc + tk.start, kdst + tk.start, HV ? vsrc + tk.start : nullptr,
+                          HV ? vdst + tk.start : nullptr, tk.size);
+        } else {  // a call here costs the 64-bit base case more spills than it saves
+          for (int64_t i = threadIdx.x; i < tk.size; i += NT) {
+            kdst[tk.start + i] = ld_key<K>(ksrc + tk.start + i);
+            if constexpr (HV) vdst[tk.start + i] = ld_key<K>(vsrc + tk.start + i);
+          }
         }
         my_copy += tk.size;
       }
@@ -1658,16 +1871,25 @@ __device__ void phase_merge_prep(const Params &P, int level, unsigned char *smem
   long long *sh = (long long *)dts_smem;
   for (int64_t zi = z0 + blockIdx.x; zi < z1; zi += gridDim.x) {
     const MZone Z = ldcg_obj(&P.zones[zi]);
-    if (Z.m < 0 || Z.m > HASH_HW / 2 || Z.obuf > 1) {
+    if (Z.m < 0 || Z.m > HASH_HW / 2 || Z.obuf > 1 || Z.np > Z.m) {
       if (threadIdx.x == 0) check_failed(P, 8, zi, Z.m);
       continue;
     }
-    const K *B0 = (const K *)P.keys[Z.obuf ^ 1] + Z.zs;
     const int q = threadIdx.x;
     long long sz = 0, lb = 0;
+    K key = (K)0;
     if (q < Z.m) {
-      const K key = ld_key<K>((const K *)P.mh_keys + Z.mh + q);
+      key = ld_key<K>((const K *)P.mh_keys + Z.mh + q);
       sz = __ldcg((const long long *)&P.mh_sizes[Z.mh + q]);
+    }
+    long long tot;
+    const long long pre = block_excl_scan<long long>(sz, sh, tot);
+    // the light bucket follows the np heavy runs stored before it
+    if (q == Z.np) sh[NWARP + 2] = pre;
+    __syncthreads();
+    const long long lof = Z.np < Z.m ? sh[NWARP + 2] : tot;
+    const K *B0 = (const K *)P.keys[Z.obuf ^ 1] + Z.zs + lof;
+    if (q < Z.m) {
       int64_t a = 0, b = Z.b0;
       while (a < b) {
         const int64_t mid = (a + b) >> 1;
@@ -1675,18 +1897,18 @@ __device__ void phase_merge_prep(const Params &P, int level, unsigned char *smem
         else b = mid;
       }
       lb = a;
+      P.mh_start[Z.mh + q] = Z.zs + lb + pre;
     }
-    long long tot;
-    const long long pre = block_excl_scan<long long>(sz, sh, tot);
-    if (q < Z.m) P.mh_start[Z.mh + q] = Z.zs + lb + pre;
     __syncthreads();
   }
 }
 
 // Generic merging, the comparison for Alg. 3: in each zone the sorted light
-// bucket A = [zs, zs + b0) and the concatenation B = [zs + b0, ze) of the
-// heavy buckets (sorted: they are numbered by key) are merged stably by merge
-// path, A first on equal keys, with key comparisons only.  A work item of
+// bucket A (b0 records after the np heavy runs stored before it) and the
+// concatenation B of the heavy buckets (sorted: they are numbered by key; the
+// light bucket's b0 records sit between B's first lof and the rest) are
+// merged stably by merge path, A first on equal keys, with key comparisons
+// only.  A work item of
 // MERGE_CHUNK outputs is cut into sub-tiles of MERGE_SUB; the split of every
 // sub-tile boundary d (how many of the zone's first d outputs come from A) is
 // found by one warp with a 32-ary search; each sub-tile's inputs are staged in
@@ -1695,16 +1917,19 @@ __device__ void phase_merge_prep(const Params &P, int level, unsigned char *smem
 
 // First i in [max(0, d - nb), min(d, na)] with B[d - 1 - i] < A[i] (the upper
 // end when none): a warp probes 32 evenly spaced candidates per round (the
-// predicate is monotone in i).  Every lane returns the split.
+// predicate is monotone in i).  Every lane returns the split.  B[j] is
+// Bp[j], or Bp[j + gap] from j = bsplit on.
 template <typename K>
-__device__ __forceinline__ int64_t merge_split_warp(const K *A, int64_t na, const K *B,
-                                                    int64_t nb, int64_t d, int lane) {
+__device__ __forceinline__ int64_t merge_split_warp(const K *A, int64_t na, const K *Bp,
+                                                    int64_t bsplit, int64_t gap, int64_t nb,
+                                                    int64_t d, int lane) {
   int64_t lo = d > nb ? d - nb : 0, hi = d < na ? d : na;
   while (lo < hi) {
     const int64_t step = (hi - lo + 31) / 32;
     const int64_t p = lo + (int64_t)lane * step;
     bool before = false;  // A[p] is among the first d outputs
-    if (p < hi) before = !(ld_key<K>(B + (d - 1 - p)) < ld_key<K>(A + p));
+    const int64_t jb = d - 1 - p;
+    if (p < hi) before = !(ld_key<K>(Bp + jb + (jb < bsplit ? 0 : gap)) < ld_key<K>(A + p));
     const int cnt = __popc(__ballot_sync(0xffffffffu, before));  // lanes 0..cnt-1
     const int64_t nlo = cnt > 0 ? lo + (int64_t)(cnt - 1) * step + 1 : lo;
     const int64_t pc = lo + (int64_t)cnt * step;
@@ -1732,6 +1957,7 @@ __device__ void phase_merge_generic(const Params &P, int level) {
   uint16_t *sidx = cv.take<uint16_t>(MERGE_SUB);
   long long *spl = cv.take<long long>(NSUB + 1);
   MZone *Zs = cv.take<MZone>(1);
+  long long *lof_sh = cv.take<long long>(1);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   long long my = 0;
   int64_t curz = -1;
@@ -1744,15 +1970,24 @@ __device__ void phase_merge_generic(const Params &P, int level) {
     }
     if (a != curz) {
       __syncthreads();
-      if (threadIdx.x == 0) *Zs = ldcg_obj(&P.zones[a]);
+      if (threadIdx.x == 0) {
+        *Zs = ldcg_obj(&P.zones[a]);
+        // records of the heavy runs stored before the light bucket
+        long long lof = 0;
+        for (int q = 0; q < Zs->np && q < Zs->m; ++q)
+          lof += __ldcg((const long long *)&P.mh_sizes[Zs->mh + q]);
+        *lof_sh = lof;
+      }
       __syncthreads();
       curz = a;
     }
     const MZone Z = *Zs;
+    const int64_t lof = *lof_sh;
     const int64_t na = Z.b0, nb = Z.ze - Z.zs - Z.b0;
     const int64_t o0 = Z.zs + (ch - Z.chunk0) * MERGE_CHUNK;
     const int64_t o1 = o0 + MERGE_CHUNK < Z.ze ? o0 + MERGE_CHUNK : Z.ze;
-    if (Z.obuf > 1 || na < 0 || nb < 0 || ch < Z.chunk0 || o0 >= o1) {
+    if (Z.obuf > 1 || na < 0 || nb < 0 || ch < Z.chunk0 || o0 >= o1 || Z.np > Z.m ||
+        lof < 0 || lof > nb) {
       if (threadIdx.x == 0) latch(P, ERR_INTERNAL);
       __syncthreads();
       continue;
@@ -1765,7 +2000,8 @@ __device__ void phase_merge_generic(const Params &P, int level) {
     const int ns = (int)((o1 - o0 + MERGE_SUB - 1) / MERGE_SUB);
     if (w <= ns) {
       const int64_t e = o0 + (int64_t)w * MERGE_SUB < o1 ? o0 + (int64_t)w * MERGE_SUB : o1;
-      const int64_t sp = merge_split_warp<K>(kin + Z.zs, na, kin + Z.zs + Z.b0, nb, e - Z.zs, lane);
+      const int64_t sp =
+          merge_split_warp<K>(kin + Z.zs + lof, na, kin + Z.zs, lof, na, nb, e - Z.zs, lane);
       if (lane == 0) spl[w] = sp;
     }
     __syncthreads();
@@ -1781,7 +2017,8 @@ __device__ void phase_merge_generic(const Params &P, int level) {
       }
       const int la = (int)(i1 - i0), lb = (int)(j1 - j0);  // la + lb = n2
       for (int q = threadIdx.x; q < n2; q += NT) {
-        const int64_t g = q < la ? Z.zs + i0 + q : Z.zs + Z.b0 + j0 + (q - la);
+        const int64_t jb = j0 + (q - la);
+        const int64_t g = q < la ? Z.zs + lof + i0 + q : Z.zs + jb + (jb < lof ? 0 : Z.b0);
         sk[q] = ld_key<K>(kin + g);
         if constexpr (HV) sv[q] = ld_key<K>(vin + g);
       }
@@ -1833,6 +2070,7 @@ __device__ void phase_merge(const Params &P, int level, unsigned char *smem) {
   long long *hp = cv.take<long long>(HASH_HW / 2 + 1);
   long long *sh = cv.take<long long>(NWARP + 1);
   MZone *Zs = cv.take<MZone>(1);
+  long long *lof_sh = cv.take<long long>(1);
   long long my = 0;
   int64_t curz = -1;
   for (int64_t ch = c0 + blockIdx.x; ch < c1; ch += gridDim.x) {
@@ -1848,7 +2086,7 @@ __device__ void phase_merge(const Params &P, int level, unsigned char *smem) {
       __syncthreads();
       const int q = threadIdx.x;
       long long sz = 0;
-      if (Zs->m < 0 || Zs->m > HASH_HW / 2) {
+      if (Zs->m < 0 || Zs->m > HASH_HW / 2 || Zs->np > Zs->m) {
         if (q == 0) check_failed(P, 8, a, Zs->m);
         __syncthreads();
         if (q == 0) Zs->m = 0;
@@ -1862,10 +2100,13 @@ __device__ void phase_merge(const Params &P, int level, unsigned char *smem) {
       long long tot;
       const long long pre = block_excl_scan<long long>(sz, sh, tot);
       if (q < Zs->m) hp[q] = pre;
+      // input offset of the light bucket: the heavy runs stored before it
+      if (q == Zs->np) *lof_sh = q < Zs->m ? pre : tot;
       __syncthreads();
       curz = a;
     }
     const MZone &Z = *Zs;
+    const int64_t lof = *lof_sh;
     const int ib = Z.obuf ^ 1;
     const K *kin = (const K *)P.keys[ib];
     K *kout = (K *)P.keys[Z.obuf];
@@ -1900,10 +2141,10 @@ __device__ void phase_merge(const Params &P, int level, unsigned char *smem) {
           const int i = cnt - 1;
           int64_t f;
           if (i >= 0 && pp < hs[i] + hz[i]) {
-            f = Z.zs + Z.b0 + hp[i] + (pp - hs[i]);
+            f = Z.zs + (i < Z.np ? 0 : Z.b0) + hp[i] + (pp - hs[i]);
           } else {
             const int64_t before = i >= 0 ? hp[i] + hz[i] : 0;
-            f = pp - before;
+            f = pp - before + lof;
           }
           if (f >= Z.zs && f < Z.ze) from[r] = f;
           else latch(P, ERR_INTERNAL);
@@ -1981,6 +2222,7 @@ __device__ __forceinline__ void write_stats(const Params &P, unsigned long long 
     d->learned_used = learned_level(P, 0) ? 1 : 0;
     d->learned_est[0] = P.lrn_est ? P.lrn_est[0] : 0.0;
     d->learned_est[1] = P.lrn_est ? P.lrn_est[1] : 0.0;
+    d->free_zones = ld_cg64(&c->st_free_zones);
     d->check_site = ld_cg64(&c->dbg[0]);
     d->check_values[0] = ld_cg64(&c->dbg[1]);
     d->check_values[1] = ld_cg64(&c->dbg[2]);
