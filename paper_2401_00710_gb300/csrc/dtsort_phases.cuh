@@ -64,6 +64,18 @@ struct Carve {
   }
 };
 
+// Copy runs whose task descriptors the whole CTA writes later (a heavy run
+// can be 10^8 records: thousands of tasks for the one thread that finds it).
+struct CopyReq {
+  int64_t start, size, i0, k;
+  int32_t src, dst;
+};
+constexpr int COPY_REQS = 128;
+struct CopyList {
+  CopyReq *req;
+  int *n;
+};
+
 // Threads of the per-phase scatter kernel: one CTA of 1024 per SM, tiles of
 // 1024 * ITEMS records.  Twice the records per tile give each bucket run of a
 // tile twice the length, so half as many partly written 32-byte sectors per
@@ -133,7 +145,7 @@ constexpr size_t phase_smem_bytes(int ph) {
                      16 + 512;
   // bucket scan: counts, offsets, light table
   const size_t scan = 16 + 8 * NB_PAD + 16 + 8 * (NB_PAD + 1) + 16 + 4 * ((1 << GAMMA_HW) + 1) +
-                      16 + 8 * (NWARP + 1) + 256;
+                      16 + 8 * (NWARP + 1) + 16 + sizeof(CopyReq) * COPY_REQS + 16 + 4 + 256;
   switch (ph) {
     case 2: return smp;                        // KP_SAMPLE
     case 3: return hist;                       // KP_HIST
@@ -180,28 +192,54 @@ __device__ __forceinline__ void push_task(const Params &P, const Task &t) {
   P.tasks[i] = t;
 }
 
+// Task q of the copy run [start, start + size) reserved at i0.
+__device__ __forceinline__ void write_copy_task(const Params &P, int64_t start, int64_t size,
+                                                int src, int dst, long long i0, long long q) {
+  if (i0 + q >= P.tmax) {
+    latch(P, ERR_INTERNAL);
+    return;
+  }
+  const int64_t a = q * COPY_CHUNK;
+  Task t;
+  t.start = start + a;
+  t.size = size - a < COPY_CHUNK ? size - a : COPY_CHUNK;
+  t.base = 0;
+  t.hi = 0;
+  t.src = (uint8_t)src;
+  t.dst = (uint8_t)dst;
+  t.kind = TASK_COPY;
+  P.tasks[i0 + q] = t;
+}
+
+// All of the run's tasks are reserved at once; with a list, a run of more
+// than one task is left there for flush_copies.
 __device__ __forceinline__ void push_copy(const Params &P, int64_t start, int64_t size,
-                                          int src, int dst) {
+                                          int src, int dst, const CopyList *L = nullptr) {
   if (size <= 0 || src == dst) return;
-  // all of the run's tasks reserved at once (a heavy run can be 10^8 records)
   const long long k = (size + COPY_CHUNK - 1) / COPY_CHUNK;
   const long long i0 = atomic_add_ll(&P.ctl->ntasks, k);
-  for (long long q = 0; q < k; ++q) {
-    if (i0 + q >= P.tmax) {
-      latch(P, ERR_INTERNAL);
+  if (L && k > 1) {
+    const int r = atomicAdd(L->n, 1);
+    if (r < COPY_REQS) {
+      L->req[r] = CopyReq{start, size, i0, k, src, dst};
       return;
     }
-    const int64_t a = q * COPY_CHUNK;
-    Task t;
-    t.start = start + a;
-    t.size = size - a < COPY_CHUNK ? size - a : COPY_CHUNK;
-    t.base = 0;
-    t.hi = 0;
-    t.src = (uint8_t)src;
-    t.dst = (uint8_t)dst;
-    t.kind = TASK_COPY;
-    P.tasks[i0 + q] = t;
   }
+  for (long long q = 0; q < k; ++q) write_copy_task(P, start, size, src, dst, i0, q);
+}
+
+// The whole CTA writes the descriptors of the listed runs and empties the
+// list (all threads call; the list's writers are done).
+__device__ __forceinline__ void flush_copies(const Params &P, const CopyList &L) {
+  __syncthreads();
+  const int nr = min(*L.n, COPY_REQS);
+  for (int r = 0; r < nr; ++r) {
+    const CopyReq q = L.req[r];
+    for (long long t = threadIdx.x; t < q.k; t += NT)
+      write_copy_task(P, q.start, q.size, q.src, q.dst, q.i0, t);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) *L.n = 0;
 }
 
 __device__ __forceinline__ void push_seg(const Params &P, int list, const Seg &s) {
@@ -216,10 +254,11 @@ __device__ __forceinline__ void push_seg(const Params &P, int list, const Seg &s
 // A bucket that still needs work: recurse, sort on chip, or just move it.
 __device__ __forceinline__ void emit_child(const Params &P, int next_list, int64_t start,
                                            int64_t size, int hi, uint64_t base, int data_buf,
-                                           int res_buf, int64_t ntotal) {
+                                           int res_buf, int64_t ntotal,
+                                           const CopyList *L = nullptr) {
   if (size <= 0) return;
   if (hi == 0 || size == 1) {
-    push_copy(P, start, size, data_buf, res_buf);
+    push_copy(P, start, size, data_buf, res_buf, L);
   } else if (size <= P.cap) {
     Task t;
     t.start = start;
@@ -849,6 +888,9 @@ __device__ void phase_scan(const Params &P, int level, unsigned char *smem) {
   long long *excl = cv.take<long long>(NB_PAD + 1);
   int32_t *lid_s = cv.take<int32_t>((1 << GAMMA_HW) + 1);
   long long *sh = cv.take<long long>(NWARP + 1);
+  CopyList CL{cv.take<CopyReq>(COPY_REQS), cv.take<int>(1)};
+  if (threadIdx.x == 0) *CL.n = 0;
+  __syncthreads();
   for (int64_t si = blockIdx.x; si < nseg; si += gridDim.x) {
     const Seg S = ldcg_obj(&P.segs[p][si]);
     const SegInfo I = ldcg_obj(&P.info[si]);
@@ -914,16 +956,16 @@ __device__ void phase_scan(const Params &P, int level, unsigned char *smem) {
           else latch(P, ERR_INTERNAL);
           // heavy runs must sit in the merge's input buffer
           if (dstb == res) {
-            push_copy(P, zs, ls - zs, dstb, dstb ^ 1);
-            push_copy(P, ls + b0, ze - ls - b0, dstb, dstb ^ 1);
+            push_copy(P, zs, ls - zs, dstb, dstb ^ 1, &CL);
+            push_copy(P, ls + b0, ze - ls - b0, dstb, dstb ^ 1, &CL);
           }
         } else {
           // the zone's runs are already in key order: the light bucket's
           // result and the heavy runs go straight to the required buffer
           free_zones += 1;
           if (dstb != res) {
-            push_copy(P, zs, ls - zs, dstb, res);
-            push_copy(P, ls + b0, ze - ls - b0, dstb, res);
+            push_copy(P, zs, ls - zs, dstb, res, &CL);
+            push_copy(P, ls + b0, ze - ls - b0, dstb, res, &CL);
           }
         }
       }
@@ -939,7 +981,7 @@ __device__ void phase_scan(const Params &P, int level, unsigned char *smem) {
         cbase = a;
         chi = top >= a ? bitlen64(top - a) : 0;
       }
-      emit_child(P, p ^ 1, ls, b0, chi, cbase, dstb, light_res, S.ntotal);
+      emit_child(P, p ^ 1, ls, b0, chi, cbase, dstb, light_res, S.ntotal, &CL);
       if (level == 0 && si == 0) {
         atomicAdd(&c->st_bsum, (double)b0);
         atomicAdd(&c->st_bsq, (double)b0 * (double)b0);
@@ -951,13 +993,13 @@ __device__ void phase_scan(const Params &P, int level, unsigned char *smem) {
       const int ob = nb - 1;
       const int64_t os = S.start + excl[ob], ol = cntv[ob];
       if (ol > 0) {
-        emit_child(P, p ^ 1, os, ol, S.hi, S.base, dstb, res, S.ntotal);
+        emit_child(P, p ^ 1, os, ol, S.hi, S.base, dstb, res, S.ntotal, &CL);
         atomic_add_ll(&c->st_overflow[level < 15 ? level : 15], (long long)ol);
       }
     }
     if (heavy_recs) atomic_add_ll(&c->st_heavy_records[level < 15 ? level : 15], heavy_recs);
     if (free_zones) atomic_add_ll(&c->st_free_zones, free_zones);
-    __syncthreads();
+    flush_copies(P, CL);
   }
 }
 
