@@ -393,6 +393,30 @@ def test_unsampled_light_key_outside_the_layout_forces_the_merge(G, dtype, side)
     check(G, keys, None)
 
 
+def test_heavy_min_share(G):
+    # Zipf 1.0 ranks: the keys detected at the root hold a minority of the
+    # sample, so by default (250 thousandths) the root keeps none and is
+    # distributed by its digit; -1 keeps any share (the paper's rule).  The
+    # output is the same stable order either way.
+    n = 3_000_000
+    keys = gen.family("zipf1.0", n, np.uint32, seed=5)
+    vals = gen.iota(n, np.uint32)
+    st = check(G, keys, vals)
+    assert st["heavy_keys"][0] == 0
+    G.set_options(heavy_min_share=-1)
+    st = check(G, keys, vals)
+    assert st["heavy_keys"][0] > 0
+    G.set_options(heavy_min_share=1000)  # only a one-key subproblem keeps its key
+    st = check(G, keys, vals)
+    assert st["heavy_keys"][0] == 0
+    for bad in (-2, 1001):
+        o = dts.dtsort_default_options()
+        o.heavy_min_share = bad
+        with pytest.raises(dts.DtsortError) as e:
+            dts.dtsort_set_options(G.h, o)
+        assert e.value.status == dts.DTSORT_ERR_INVALID_ARG
+
+
 def test_deterministic(G):
     n = 1_000_000
     keys = gen.family("zipf1.0", n, np.uint32, seed=21)
