@@ -394,21 +394,21 @@ def test_unsampled_light_key_outside_the_layout_forces_the_merge(G, dtype, side)
 
 
 def test_heavy_min_share(G):
-    # Zipf 1.0 ranks: the keys detected at the root hold a minority of the
-    # sample, so by default (250 thousandths) the root keeps none and is
-    # distributed by its digit; -1 keeps any share (the paper's rule).  The
-    # output is the same stable order either way.
+    # one key holding 15% of the records among uniform ones: below the default
+    # minimum share (250 thousandths of the sample) the root keeps no heavy
+    # key and distributes it by its digit; -1 keeps any share (the paper's
+    # rule), 1000 none.  At 40% the default keeps it.  The output is the same
+    # stable order in every case.
     n = 3_000_000
-    keys = gen.family("zipf1.0", n, np.uint32, seed=5)
+    rng = np.random.default_rng(9)
     vals = gen.iota(n, np.uint32)
-    st = check(G, keys, vals)
-    assert st["heavy_keys"][0] == 0
-    G.set_options(heavy_min_share=-1)
-    st = check(G, keys, vals)
-    assert st["heavy_keys"][0] > 0
-    G.set_options(heavy_min_share=1000)  # only a one-key subproblem keeps its key
-    st = check(G, keys, vals)
-    assert st["heavy_keys"][0] == 0
+    for share, expect in ((0.15, {0: 0, -1: 1, 1000: 0}), (0.40, {0: 1, -1: 1, 1000: 0})):
+        keys = rng.integers(0, 1 << 32, size=n, dtype=np.uint64).astype(np.uint32)
+        keys[rng.random(n) < share] = 12345
+        for hms, nh in expect.items():
+            G.set_options(heavy_min_share=hms)
+            st = check(G, keys, vals)
+            assert st["heavy_keys"][0] == nh, (share, hms, st["heavy_keys"][:3])
     for bad in (-2, 1001):
         o = dts.dtsort_default_options()
         o.heavy_min_share = bad
