@@ -53,7 +53,9 @@ def check_full(G, name, dtype, bucketing=None):
     return st
 
 
-@pytest.mark.parametrize("name", ["uniform", "zipf1.2", "exp", "bitexp", "distinct10"])
+@pytest.mark.parametrize("name", ["uniform", "zipf0.8", "zipf1.0", "zipf1.2", "zipf1.5",
+                                  "zipf1.2hash", "exp", "bitexp", "distinct10", "bexp30",
+                                  "unif1e3", "edges"])
 def test_full_u32_kv(G, name):
     st = check_full(G, name, np.uint32)
     if name == "uniform":
